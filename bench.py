@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark: one timestep of the grey radiative LB scheme (stream + exact
+implicit collision) on the radiating-sphere workload, 128^3 sites x 42
+directions (icosahedral geodesic level 1), float32 populations, vacuum
+faces, kappa_a = eta = 40 inside R = 0.25 (kappa_a R = 10), cfl 0.5.
+
+Prints one JSON line.  `value` is site-direction updates per second over
+the timed steps (inputs resident in HBM, 705 MB of populations per step,
+larger than L2); `e2e` is the same metric through the C ABI with host
+buffers: every step copies new fluid coefficients (kappa_a, eta) from pinned
+host memory, steps, and reads E and F back to the host, as a coupled
+hydrodynamics code does each step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun) runs independent replicas, one per GPU (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 128
+LEVEL = 1
+NDIR = 42
+KAPPA_R = 10.0
+CFL = 0.5
+METRIC = "site-direction updates/s"
+UNIT = "sd/s"
+WORKLOAD = "3D radiating sphere 128^3 x 42 dirs (icosahedral L1), FP32 populations, kappa_a R = 10, vacuum faces, cfl 0.5"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            v = d.get("hbm_gbs") or d.get("hbm_GBs") or d.get("hbm")
+            if v:
+                return float(v), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def _traffic_from_profiles(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary, or None when the
+    kernel source changed after the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_static_f32_sphere128_42.md")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2007_05718_gb300", "csrc", "kernels_step.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload_fields():
+    from paper_2007_05718_gb300 import workloads as W
+    return W.radiating_sphere(N_SIDE, KAPPA_R)
+
+
+def oracle_sample_time(n_side, steps=1):
+    """Time the FP64 oracle (as it stands) on an n_side^3 sub-box of the same
+    workload, single thread; returns (seconds per step, sd per step)."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import directions as D, lb
+from paper_2007_05718_gb300 import workloads as W
+n = %d
+sp = W.radiating_sphere(n, %r)
+nv, w = D.icosphere(%d)
+lat = lb.Lattice(3, (n, n, n), nv, w, cfl=%r, dx=1.0 / n, bc=(lb.VACUUM,) * 3)
+co = lb.Static(kappa_a=sp["kappa_a"].astype(float), eta=sp["eta"].astype(float))
+I = lb.isotropic(sp["E0"].astype(float), lat)
+t0 = time.perf_counter()
+for _ in range(%d):
+    I = lb.step(I, lat, co)
+dt = time.perf_counter() - t0
+print(json.dumps({"sec": dt / %d, "sd": n ** 3 * len(w)}))
+""" % (ROOT, n_side, KAPPA_R, LEVEL, CFL, steps, steps)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["sec"], d["sd"]
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n_sample = 48
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle_sample_time(16, 1)
+    sec, sd = oracle_sample_time(n_sample, max(args.steps, 1))
+    value = sd / sec
+    ncores = len(os.sched_getaffinity(0))
+    sample = "%d^3 sub-box of the same workload (42 dirs), %d oracle steps, FP64 numpy, 1 thread" % (
+        n_sample, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sites": N_SIDE ** 3, "ndir": NDIR},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "host_cores": ncores},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    ws, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2007_05718_gb300 import build, lbrt
+    build.build()
+    sp = _workload_fields()
+    stream = torch.cuda.Stream()
+    sites = N_SIDE ** 3
+    with torch.cuda.stream(stream):
+        h = lbrt.lb_rt_create(3, N_SIDE, N_SIDE, N_SIDE, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL,
+                              cfl=CFL, dx=1.0 / N_SIDE, bc=(lbrt.LB_RT_VACUUM,) * 3,
+                              stream=stream.cuda_stream)
+        ka = torch.from_numpy(sp["kappa_a"]).cuda()
+        eta = torch.from_numpy(sp["eta"]).cuda()
+        E0 = torch.from_numpy(sp["E0"]).cuda()
+        lbrt.lb_rt_set_fluid(h, kappa_a=ka, eta=eta)
+        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        # warm-up
+        lbrt.lb_rt_step(h, args.warmup)
+        stream.synchronize()
+        _barrier(ws)
+        clocks = Clocks(local)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        t0.record(stream)
+        for _ in range(args.steps):
+            lbrt.lb_rt_step(h, 1)
+        t1.record(stream)
+        t1.synchronize()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        ms = t0.elapsed_time(t1)
+        ck = clocks.stop()
+        ms_max = _max_over_ranks(ws, ms)
+        ms_step = ms_max / args.steps
+        sd_step = sites * N
+        value = sd_step * ws / (ms_max * 1e-3 / args.steps)
+
+        # end to end through the C ABI with host buffers
+        ka_h = torch.from_numpy(sp["kappa_a"]).pin_memory()
+        eta_h = torch.from_numpy(sp["eta"]).pin_memory()
+        E_h = torch.empty(sites, dtype=torch.float32).pin_memory()
+        F_h = torch.empty((3, sites), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
+            lbrt.lb_rt_step(h, 1)
+            lbrt.lb_rt_moments(h, E=E_h, F=F_h)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        te = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
+            lbrt.lb_rt_step(h, 1)
+            lbrt.lb_rt_moments(h, E=E_h, F=F_h)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - te
+        e_ms = _max_over_ranks(ws, max(e0.elapsed_time(e1), wall * 1e3))
+        e2e_value = sd_step * ws / (e_ms * 1e-3 / args.e2e_steps)
+        lbrt.lb_rt_destroy(h)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    bytes_per_launch = sites * N * 8.0 + sites * 8.0   # populations r+w, kappa_a and eta fields
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (ms_step * 1e-3) / 1e9
+    traffic = _traffic_from_profiles("step")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sites": sites, "ndir": N, "global_batch": ws,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (%.0f MB of populations per step)" % (sites * N * 4 / 1e6)},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * sites,
+                "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps},
+        "clocks": ck,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            sec, sd = oracle_sample_time(64, 1)
+            line["cpu_baseline"] = {"value": sd / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "1 oracle step (FP64 numpy) of a 64^3 sub-box of the same workload, 42 dirs",
+                                    "host_cores": len(os.sched_getaffinity(0))}
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

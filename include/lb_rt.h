@@ -1,0 +1,203 @@
+/*
+ * lb_rt.h -- C ABI of the GB300 grey radiative Lattice-Boltzmann library.
+ *
+ * The library advances the discrete specific intensities I_i(r, t) of the
+ * radiative LB equation (Weih et al. 2020, Sec. 3.2, Eqs. rte_discrete and
+ * source-and-equil) on a uniform 2D or 3D grid: every step pull-streams each
+ * direction with the trilinear (bilinear) rule of Eq. (interp), solves the
+ * implicit collision of Eq. (rte_implicit) exactly (or the explicit
+ * Eq. collision-step, or a fixed number of Lambda-iteration cycles), and can
+ * reduce the moments E, F^a, P^ab of Eqs. (moments_discrete, higher_moments).
+ * A moving background fluid uses the mixed-frame equation of App. B.
+ *
+ * Conventions shared by every call
+ *   - c = 1; dt = cfl * dx; opacities in 1/length, emissivities in E/length.
+ *   - The populations carry their quadrature weight: E = sum_i I_i.
+ *   - Site fields are float32, layout [nz][ny][nx] (x fastest), "sites" =
+ *     nx*ny*nz.  Vector fields are [3][nz][ny][nx]; populations are
+ *     direction-major [N][nz][ny][nx].
+ *   - ptr_kind = LB_RT_HOST or LB_RT_DEVICE says where a caller pointer
+ *     lives.  Device pointers must be valid on the handle's device.  Inputs
+ *     are copied into library-owned memory before the call returns (host) or
+ *     stream-ordered on the handle's stream (device): the caller may reuse
+ *     host buffers at once and device buffers after the stream reaches the
+ *     call.
+ *   - Every call returns lb_rt_status; negative values are errors and
+ *     lb_rt_last_error() gives a message.  No call throws.  A handle is
+ *     bound to one CUDA stream and is not thread-safe.
+ *   - lb_rt_step() only enqueues work; errors raised on the device surface
+ *     on the next lb_rt_sync(), lb_rt_moments() or lb_rt_get_*() call.
+ */
+#ifndef LB_RT_H
+#define LB_RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_rt lb_rt;
+
+typedef enum {
+  LB_RT_OK = 0,
+  LB_RT_EINVAL = -1,    /* bad argument or configuration */
+  LB_RT_ENOMEM = -2,    /* device or host allocation failed */
+  LB_RT_ECUDA = -3,     /* a CUDA runtime call failed */
+  LB_RT_ETIMEDOUT = -4, /* a bounded device wait gave up */
+  LB_RT_ESTATE = -5     /* call not valid in the handle's current state */
+} lb_rt_status;
+
+/* built-in direction sets (used when lb_rt_config.dirs == NULL) */
+enum {
+  LB_RT_RING2D = 1,          /* N equally spaced on the circle, phi_k = ring_offset + 2 pi k/N,
+                                w = 1/N (Sec. 3.2.1, 2D quadrature of order N-1) */
+  LB_RT_ICOSPHERE = 2,       /* icosahedral geodesic set, level = dirset_param[0]:
+                                10*4^level + 2 points, w = 1/N */
+  LB_RT_GAUSS_LEGENDRE = 3   /* Gauss-Legendre (dirset_param[0] nodes in cos theta) x
+                                trapezoid (dirset_param[1] points in phi) product rule
+                                (Sec. 3.2.1) */
+};
+
+enum { LB_RT_PERIODIC = 0, LB_RT_VACUUM = 1 };               /* per-axis boundary */
+enum { LB_RT_F32 = 0, LB_RT_F16_DEV = 1, LB_RT_BF16_DEV = 2 }; /* population storage */
+enum {
+  LB_RT_IMPLICIT_EXACT = 0,  /* exact solution of Eq. (rte_implicit) */
+  LB_RT_EXPLICIT = 1,        /* Eq. (collision-step) */
+  LB_RT_LAMBDA_K = 2         /* lambda_iters cycles of the Lambda iteration (Sec. 3.3) */
+};
+enum { LB_RT_HOST = 0, LB_RT_DEVICE = 1 };
+enum {
+  LB_RT_STATE_POPULATIONS = 0, /* N*sites floats, direction-major */
+  LB_RT_STATE_ISOTROPIC = 1,   /* sites floats E0: I_i = w_i E0 */
+  LB_RT_STATE_P1 = 2           /* 4*sites floats (E0, F0x, F0y, F0z): I_i = w_i (E0 + d n_i.F0) */
+};
+
+/* Maximum number of directions a handle accepts. */
+#define LB_RT_MAX_DIRS 192
+
+typedef struct {
+  int dims;                /* 2 or 3 */
+  int nx, ny, nz;          /* grid; nz must be 1 when dims == 2 */
+  int ndir;                /* N when dirs != NULL (or for LB_RT_RING2D); else derived */
+  const double* dirs;      /* N*3 unit vectors, caller-owned, copied at create; or NULL */
+  const double* weights;   /* N weights (NULL => 1/N); used only with dirs */
+  int dirset;              /* built-in set when dirs == NULL */
+  int dirset_param[2];     /* see the LB_RT_ICOSPHERE / LB_RT_GAUSS_LEGENDRE comments */
+  double ring_offset;      /* phi_0 of LB_RT_RING2D, radians */
+  double cfl;              /* c dt / dx, 0 < cfl <= 1 (keeps the weights of Eq. interp in [0,1]) */
+  double dx;               /* cell size */
+  int bc[3];               /* per axis x, y, z: LB_RT_PERIODIC or LB_RT_VACUUM (reads 0 outside) */
+  int storage;             /* LB_RT_F32 | LB_RT_F16_DEV | LB_RT_BF16_DEV */
+  int collision;           /* LB_RT_IMPLICIT_EXACT | LB_RT_EXPLICIT | LB_RT_LAMBDA_K */
+  int lambda_iters;        /* cycles for LB_RT_LAMBDA_K (the paper's timing runs use 5) */
+  int moving;              /* 0: static fluid; 1: mixed-frame moving fluid (App. B) */
+  int budget;              /* 1: accumulate the FP64 energy budget every step */
+  void* stream;            /* cudaStream_t to run on; NULL => the library creates one */
+} lb_rt_config;
+
+/* Fluid coefficients.  For each site field, a NULL pointer means "uniform,
+ * use the scalar next to it".
+ * Static fluid (Eq. rte_gray_bgkform): absorption kappa_a, scattering
+ * kappa_0, lambda = 3 kappa_1 / kappa_0, emissivity eta.
+ * Moving fluid (App. B, kappa_1 = 0): three-velocity v ([3][sites], |v| < 1;
+ * NULL => at rest), fluid-frame kt_a, kt_0 and eta_t. */
+typedef struct {
+  const float* kappa_a; float kappa_a_s;
+  const float* kappa_0; float kappa_0_s;
+  const float* lambda;  float lambda_s;
+  const float* eta;     float eta_s;
+  const float* v;
+  const float* kt_a;    float kt_a_s;
+  const float* kt_0;    float kt_0_s;
+  const float* eta_t;   float eta_t_s;
+} lb_rt_fluid;
+
+/* Energy budget in FP64, summed since the last lb_rt_set_state()
+ * (all quantities are sums over sites of E = sum_i I_i):
+ *   total     current sum E
+ *   initial   sum E right after lb_rt_set_state()
+ *   outflow   sum over steps of (sum E^n - sum E*): what streaming moved out of
+ *             the domain through vacuum faces
+ *   source    sum over steps of (sum E_collided - sum E*): net emission minus
+ *             absorption of the collision, dt sum (eta - kappa_a E^{n+1}) for a
+ *             static fluid
+ *   injection sum over steps of what frozen cells added over the collided values
+ * so that total - initial = source - outflow + injection up to rounding. */
+typedef struct {
+  double total, initial, outflow, source, injection;
+  long long steps;
+} lb_rt_budget;
+
+/* Create a handle: validates the configuration, builds the direction table
+ * (Sec. 3.2.1), allocates device state (two population buffers, fields) and
+ * sets I = 0, kappa = eta = 0.  Errors: EINVAL (bad config), ENOMEM, ECUDA. */
+lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out);
+
+/* Copy fluid coefficients (static or moving, per the handle's config) into
+ * library storage.  Takes effect for the next lb_rt_step().  Errors: EINVAL
+ * (NULL handle/fields, moving fields on a static handle or the reverse). */
+lb_rt_status lb_rt_set_fluid(lb_rt* h, const lb_rt_fluid* f, int ptr_kind);
+
+/* Set the populations (kind = LB_RT_STATE_*), reset the step counter and the
+ * energy budget.  In the reduced-precision storage modes the populations are
+ * encoded on the device (equilibrium-deviation form). */
+lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind);
+
+/* Frozen (prescribed) cells: after every collision the populations of
+ * cells[k] (linear site index z*ny*nx + y*nx + x) are overwritten by
+ * values[k*N + i] (Sec. 4.1.1, injected and frozen beam regions).
+ * ncells == 0 clears the list.  Arrays are host arrays, copied. */
+lb_rt_status lb_rt_set_frozen(lb_rt* h, const int64_t* cells, int ncells, const float* values);
+
+/* Enqueue nsteps timesteps on the handle's stream (stream, collide, frozen
+ * overwrite, budget).  nsteps >= 0.  Returns launch errors only. */
+lb_rt_status lb_rt_step(lb_rt* h, int nsteps);
+
+/* Moments of the current populations (Eqs. moments_discrete, higher_moments):
+ * E [sites], F [3][sites] (z component 0 in 2D), P [6][sites] in the order
+ * xx, xy, xz, yy, yz, zz.  Any output pointer may be NULL.  budget (host
+ * pointer or NULL) receives the FP64 energy budget (zeros unless
+ * config.budget = 1).  With host pointers the call synchronises the stream. */
+lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P,
+                           lb_rt_budget* budget, int ptr_kind);
+
+/* Decoded float32 populations, direction-major [N][sites]. */
+lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind);
+
+/* Checkpoint: raw device state (populations in their storage format, the
+ * per-site moment field of the reduced-precision modes, step counter and
+ * budget).  lb_rt_state_bytes() gives the size; buf is a host buffer.
+ * lb_rt_restore_state() puts it back bit for bit. */
+size_t lb_rt_state_bytes(const lb_rt* h);
+lb_rt_status lb_rt_save_state(lb_rt* h, void* buf, size_t bytes);
+lb_rt_status lb_rt_restore_state(lb_rt* h, const void* buf, size_t bytes);
+
+/* Wait for the handle's stream; returns the first device-side or CUDA error. */
+lb_rt_status lb_rt_sync(lb_rt* h);
+
+/* Direction table in the canonical order the library uses: dirs [N*3],
+ * weights [N], signs [N*3] (sgn(n) with sgn(0) = +1, the upwind side of
+ * Eq. interp).  Any pointer may be NULL.  Host pointers. */
+lb_rt_status lb_rt_directions(const lb_rt* h, int* ndir, double* dirs, double* weights,
+                              int8_t* signs);
+
+/* Time of the last lb_rt_step() batch's step kernels, measured with CUDA
+ * events on the handle's stream (ms per step kernel, summed over the batch)
+ * -- valid after lb_rt_sync(). Returns EINVAL if timing was not enabled. */
+lb_rt_status lb_rt_enable_timing(lb_rt* h, int on);
+lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch);
+
+/* Message of the last error on h; with h == NULL, why the calling thread's
+ * last lb_rt_create() failed. */
+const char* lb_rt_last_error(const lb_rt* h);
+const char* lb_rt_version(void);
+
+/* NULL-safe; frees every device and host resource of the handle. */
+void lb_rt_destroy(lb_rt* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_RT_H */

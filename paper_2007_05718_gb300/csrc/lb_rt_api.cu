@@ -1,0 +1,584 @@
+// Host side of the C ABI declared in include/lb_rt.h: validation, device
+// memory, the direction table handed to the kernels, and the per-step launch
+// sequence (step kernel -> frozen overwrite -> FP64 budget finalisation).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lb_rt_internal.h"
+
+using namespace lbrt;
+
+struct lb_rt {
+  lb_rt_config cfg{};
+  Grid grid{};
+  int N = 0;
+  double dt = 0.0;
+  std::vector<double> n, w;
+  DirTable table{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  void* pop[2] = {nullptr, nullptr};
+  float4* ef[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t pop_bytes = 0;
+  // coefficient fields: static ka, k0, lam, eta (slots 0-3); moving v(3), kta, kt0, etat (4-7)
+  float* fld[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  StaticCoef sc{};
+  MovingCoef mc{};
+  int64_t* frozen_cells = nullptr;
+  float* frozen_vals = nullptr;
+  int nfrozen = 0;
+  double* partials = nullptr;
+  int partials_cap = 0;
+  double* acc = nullptr;       // 8 doubles, see k_budget_finalize
+  unsigned* err = nullptr;     // device error word
+  float* scratch = nullptr;    // moments staging for host outputs [10][sites]
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timing = false;
+  float last_ms = 0.f;
+  int last_nlaunch = 0;
+  long long steps = 0;
+  std::string msg;
+};
+
+namespace {
+
+thread_local std::string g_create_msg;  // message of the last failed lb_rt_create
+
+lb_rt_status fail(lb_rt* h, lb_rt_status st, const std::string& m) {
+  if (h) h->msg = m;
+  return st;
+}
+
+lb_rt_status cuda_fail(lb_rt* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? LB_RT_ENOMEM : LB_RT_ECUDA, m);
+}
+
+#define CK(h, call)                                    \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+size_t elem_bytes(int storage) { return storage == LB_RT_F32 ? 4 : 2; }
+
+bool isotropic_table(const std::vector<double>& n, const std::vector<double>& w, int dims,
+                     std::string& why) {
+  const int N = (int)w.size();
+  double T0 = 0, T1[3] = {0, 0, 0}, T2[3][3] = {{0}};
+  for (int i = 0; i < N; ++i) {
+    T0 += w[i];
+    for (int a = 0; a < 3; ++a) {
+      T1[a] += w[i] * n[3 * i + a];
+      for (int b = 0; b < 3; ++b) T2[a][b] += w[i] * n[3 * i + a] * n[3 * i + b];
+    }
+  }
+  const double tol = 1e-10;
+  bool ok = std::fabs(T0 - 1.0) < tol;
+  for (int a = 0; a < 3; ++a) {
+    ok = ok && std::fabs(T1[a]) < tol;
+    for (int b = 0; b < 3; ++b) {
+      double want = (a == b && a < dims) ? 1.0 / dims : 0.0;
+      ok = ok && std::fabs(T2[a][b] - want) < tol;
+    }
+  }
+  if (!ok) why = "direction table is not isotropic to rank 2 (sum w = 1, sum w n = 0, sum w n n = I/d)";
+  return ok;
+}
+
+// float32 weights whose exact sum matches the FP64 sum as closely as float32
+// allows: rounding each 1/N the same way would bias sum_i w_i by up to
+// N/2 ulp, and that bias would act on the energy at every step.
+std::vector<float> balanced_weights(const std::vector<double>& w) {
+  std::vector<float> f(w.size());
+  double target = 0.0, sum = 0.0;
+  for (size_t i = 0; i < w.size(); ++i) {
+    f[i] = (float)w[i];
+    target += w[i];
+    sum += (double)f[i];
+  }
+  for (int pass = 0; pass < 4 && sum != target; ++pass) {
+    for (size_t i = 0; i < f.size() && sum != target; ++i) {
+      float g = std::nextafter(f[i], sum < target ? 2.0f : -2.0f);
+      double ns = sum - (double)f[i] + (double)g;
+      if (std::fabs(ns - target) < std::fabs(sum - target)) {
+        sum = ns;
+        f[i] = g;
+      }
+    }
+  }
+  return f;
+}
+
+void fill_table(lb_rt* h) {
+  std::memset(&h->table, 0, sizeof(h->table));
+  const std::vector<float> wf = balanced_weights(h->w);
+  for (int i = 0; i < h->N; ++i) {
+    const double* q = &h->n[3 * i];
+    h->table.nw[i] = make_float4((float)q[0], (float)q[1], (float)q[2], wf[i]);
+    int oct = (q[0] < 0 ? 1 : 0) | (q[1] < 0 ? 2 : 0) | (q[2] < 0 ? 4 : 0);
+    float octf;
+    std::memcpy(&octf, &oct, sizeof(float));
+    h->table.au[i] = make_float4((float)(h->cfg.cfl * std::fabs(q[0])),
+                                 (float)(h->cfg.cfl * std::fabs(q[1])),
+                                 (float)(h->cfg.cfl * std::fabs(q[2])), octf);
+  }
+}
+
+lb_rt_status copy_in(lb_rt* h, void* dst, const void* src, size_t bytes, int ptr_kind) {
+  if (ptr_kind != LB_RT_HOST && ptr_kind != LB_RT_DEVICE)
+    return fail(h, LB_RT_EINVAL, "ptr_kind must be LB_RT_HOST or LB_RT_DEVICE");
+  cudaMemcpyKind k = ptr_kind == LB_RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(h, cudaMemcpyAsync(dst, src, bytes, k, h->stream));
+  if (ptr_kind == LB_RT_HOST) CK(h, cudaStreamSynchronize(h->stream));
+  return LB_RT_OK;
+}
+
+lb_rt_status reset_budget(lb_rt* h) {
+  CK(h, cudaMemsetAsync(h->acc, 0, 8 * sizeof(double), h->stream));
+  cudaError_t e = launch_total_energy(h->grid, h->N, h->pop[h->cur], h->ef[h->cur],
+                                      h->cfg.storage, h->table, h->partials, h->partials_cap,
+                                      h->acc, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "total energy");
+  CK(h, cudaMemcpyAsync(h->acc + 1, h->acc, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return LB_RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_rt_version(void) { return "lbrt 0.1 (sm_103a)"; }
+
+// With a NULL handle: the reason the calling thread's last lb_rt_create failed.
+const char* lb_rt_last_error(const lb_rt* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }
+
+lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
+  if (!cfg || !out) return LB_RT_EINVAL;
+  *out = nullptr;
+  lb_rt* h = new (std::nothrow) lb_rt();
+  if (!h) return LB_RT_ENOMEM;
+  h->cfg = *cfg;
+  h->cfg.dirs = nullptr;
+  h->cfg.weights = nullptr;
+  auto bad = [&](const char* m) {
+    g_create_msg = m;
+    lb_rt_destroy(h);
+    return LB_RT_EINVAL;
+  };
+  if (cfg->dims != 2 && cfg->dims != 3) return bad("dims must be 2 or 3");
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return bad("grid sizes must be >= 1");
+  if (cfg->dims == 2 && cfg->nz != 1) return bad("dims == 2 needs nz == 1");
+  if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return bad("cfl must be in (0, 1]");
+  if (!(cfg->dx > 0.0)) return bad("dx must be > 0");
+  for (int a = 0; a < 3; ++a)
+    if (cfg->bc[a] != LB_RT_PERIODIC && cfg->bc[a] != LB_RT_VACUUM) return bad("bad bc");
+  if (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
+      cfg->storage != LB_RT_BF16_DEV)
+    return bad("bad storage");
+  if (cfg->collision != LB_RT_IMPLICIT_EXACT && cfg->collision != LB_RT_EXPLICIT &&
+      cfg->collision != LB_RT_LAMBDA_K)
+    return bad("bad collision");
+  if (cfg->collision == LB_RT_LAMBDA_K && cfg->lambda_iters < 1)
+    return bad("lambda_iters must be >= 1");
+  if (cfg->moving && cfg->collision != LB_RT_IMPLICIT_EXACT)
+    return bad("moving fluid supports the exact implicit collision only");
+  const long long sites = (long long)cfg->nx * cfg->ny * cfg->nz;
+  if (sites >= (1LL << 31)) return bad("more than 2^31 - 1 sites");
+  std::string err;
+  if (!build_directions(*cfg, h->n, h->w, err)) return bad(err.c_str());
+  h->N = (int)h->w.size();
+  if (h->N > LB_RT_MAX_DIRS) return bad("too many directions");
+  if (cfg->dims == 2)
+    for (int i = 0; i < h->N; ++i)
+      if (h->n[3 * i + 2] != 0.0) return bad("2D grids need directions with n_z == 0");
+  if (cfg->collision != LB_RT_EXPLICIT && !isotropic_table(h->n, h->w, cfg->dims, err))
+    return bad(err.c_str());
+  h->grid.nx = cfg->nx;
+  h->grid.ny = cfg->ny;
+  h->grid.nz = cfg->nz;
+  h->grid.dims = cfg->dims;
+  h->grid.sites = sites;
+  for (int a = 0; a < 3; ++a) h->grid.periodic[a] = cfg->bc[a] == LB_RT_PERIODIC;
+  h->dt = cfg->cfl * cfg->dx;
+  fill_table(h);
+
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    g_create_msg = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    lb_rt_destroy(h);
+    return LB_RT_ECUDA;
+  }
+  if (cfg->stream) {
+    h->stream = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    h->own_stream = (e == cudaSuccess);
+  }
+  h->pop_bytes = (size_t)sites * h->N * elem_bytes(cfg->storage);
+  const int max_blocks = 4096;
+  auto alloc = [&](void** p, size_t b) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(p, b);
+  };
+  alloc(&h->pop[0], h->pop_bytes);
+  alloc(&h->pop[1], h->pop_bytes);
+  if (cfg->storage != LB_RT_F32) {
+    alloc((void**)&h->ef[0], sizeof(float4) * sites);
+    alloc((void**)&h->ef[1], sizeof(float4) * sites);
+  }
+  // budget partials: one slot pair per CTA of the step kernel (grid of
+  // ceil(nx/32) x ceil(ny/4) x nz), at least max_blocks for the reductions
+  const long long step_blocks = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 3) / 4) * cfg->nz;
+  h->partials_cap = (int)std::max<long long>(max_blocks, step_blocks);
+  alloc((void**)&h->partials, sizeof(double) * 2 * h->partials_cap);
+  alloc((void**)&h->acc, sizeof(double) * 8);
+  alloc((void**)&h->err, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    g_create_msg = std::string("allocation: ") + cudaGetErrorString(e);
+    lb_rt_destroy(h);
+    return e == cudaErrorMemoryAllocation ? LB_RT_ENOMEM : LB_RT_ECUDA;
+  }
+  h->sc = StaticCoef{nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f};
+  h->mc = MovingCoef{nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, 0.f};
+  e = cudaMemsetAsync(h->pop[0], 0, h->pop_bytes, h->stream);
+  if (e == cudaSuccess && h->ef[0]) e = cudaMemsetAsync(h->ef[0], 0, sizeof(float4) * sites, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    g_create_msg = std::string("init: ") + cudaGetErrorString(e);
+    lb_rt_destroy(h);
+    return LB_RT_ECUDA;
+  }
+  *out = h;
+  return LB_RT_OK;
+}
+
+void lb_rt_destroy(lb_rt* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->pop) cudaFree(p);
+  for (void* p : h->ef) cudaFree(p);
+  for (void* p : h->fld) cudaFree(p);
+  cudaFree(h->frozen_cells);
+  cudaFree(h->frozen_vals);
+  cudaFree(h->partials);
+  cudaFree(h->acc);
+  cudaFree(h->err);
+  cudaFree(h->scratch);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+lb_rt_status lb_rt_set_fluid(lb_rt* h, const lb_rt_fluid* f, int ptr_kind) {
+  if (!h) return LB_RT_EINVAL;
+  if (!f) return fail(h, LB_RT_EINVAL, "null fluid");
+  const size_t sb = sizeof(float) * h->grid.sites;
+  auto put = [&](int slot, const float* src, size_t bytes, const float** dst) -> lb_rt_status {
+    if (!src) {
+      *dst = nullptr;
+      return LB_RT_OK;
+    }
+    if (!h->fld[slot]) CK(h, cudaMalloc((void**)&h->fld[slot], bytes));
+    lb_rt_status st = copy_in(h, h->fld[slot], src, bytes, ptr_kind);
+    *dst = h->fld[slot];
+    return st;
+  };
+  lb_rt_status st = LB_RT_OK;
+  if (!h->cfg.moving) {
+    if (f->v || f->kt_a || f->kt_0 || f->eta_t)
+      return fail(h, LB_RT_EINVAL, "moving-fluid fields given to a static handle");
+    StaticCoef c{};
+    if ((st = put(0, f->kappa_a, sb, &c.ka)) != LB_RT_OK) return st;
+    if ((st = put(1, f->kappa_0, sb, &c.k0)) != LB_RT_OK) return st;
+    if ((st = put(2, f->lambda, sb, &c.lam)) != LB_RT_OK) return st;
+    if ((st = put(3, f->eta, sb, &c.eta)) != LB_RT_OK) return st;
+    c.ka_s = f->kappa_a_s;
+    c.k0_s = f->kappa_0_s;
+    c.lam_s = f->lambda_s;
+    c.eta_s = f->eta_s;
+    h->sc = c;
+  } else {
+    if (f->kappa_a || f->kappa_0 || f->lambda || f->eta)
+      return fail(h, LB_RT_EINVAL, "static-fluid fields given to a moving handle");
+    MovingCoef c{};
+    if ((st = put(4, f->v, 3 * sb, &c.v)) != LB_RT_OK) return st;
+    if ((st = put(5, f->kt_a, sb, &c.kta)) != LB_RT_OK) return st;
+    if ((st = put(6, f->kt_0, sb, &c.kt0)) != LB_RT_OK) return st;
+    if ((st = put(7, f->eta_t, sb, &c.etat)) != LB_RT_OK) return st;
+    c.kta_s = f->kt_a_s;
+    c.kt0_s = f->kt_0_s;
+    c.etat_s = f->eta_t_s;
+    h->mc = c;
+  }
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind) {
+  if (!h) return LB_RT_EINVAL;
+  if (!data) return fail(h, LB_RT_EINVAL, "null data");
+  size_t count;
+  if (kind == LB_RT_STATE_POPULATIONS) count = (size_t)h->grid.sites * h->N;
+  else if (kind == LB_RT_STATE_ISOTROPIC) count = (size_t)h->grid.sites;
+  else if (kind == LB_RT_STATE_P1) count = 4 * (size_t)h->grid.sites;
+  else return fail(h, LB_RT_EINVAL, "bad state kind");
+  const float* src = data;
+  float* tmp = nullptr;
+  if (ptr_kind == LB_RT_HOST) {
+    CK(h, cudaMalloc((void**)&tmp, count * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(tmp, data, count * sizeof(float), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(h, e, "set_state copy");
+    }
+    src = tmp;
+  } else if (ptr_kind != LB_RT_DEVICE) {
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
+  }
+  h->cur = 0;
+  cudaError_t e = launch_init_state(h->grid, h->N, src, kind, h->pop[0], h->ef[0],
+                                    h->cfg.storage, h->table, h->stream);
+  if (tmp) {
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+  h->steps = 0;
+  return reset_budget(h);
+}
+
+lb_rt_status lb_rt_set_frozen(lb_rt* h, const int64_t* cells, int ncells, const float* values) {
+  if (!h) return LB_RT_EINVAL;
+  if (ncells < 0) return fail(h, LB_RT_EINVAL, "ncells < 0");
+  CK(h, cudaStreamSynchronize(h->stream));
+  cudaFree(h->frozen_cells);
+  cudaFree(h->frozen_vals);
+  h->frozen_cells = nullptr;
+  h->frozen_vals = nullptr;
+  h->nfrozen = 0;
+  if (ncells == 0) return LB_RT_OK;
+  if (!cells || !values) return fail(h, LB_RT_EINVAL, "null frozen arrays");
+  for (int k = 0; k < ncells; ++k)
+    if (cells[k] < 0 || cells[k] >= h->grid.sites)
+      return fail(h, LB_RT_EINVAL, "frozen cell index out of range");
+  CK(h, cudaMalloc((void**)&h->frozen_cells, sizeof(int64_t) * ncells));
+  CK(h, cudaMalloc((void**)&h->frozen_vals, sizeof(float) * ncells * (size_t)h->N));
+  CK(h, cudaMemcpy(h->frozen_cells, cells, sizeof(int64_t) * ncells, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->frozen_vals, values, sizeof(float) * ncells * (size_t)h->N,
+                   cudaMemcpyHostToDevice));
+  h->nfrozen = ncells;
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
+  if (!h) return LB_RT_EINVAL;
+  if (nsteps < 0) return fail(h, LB_RT_EINVAL, "nsteps < 0");
+  if (h->timing) CK(h, cudaEventRecord(h->ev0, h->stream));
+  int launches = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    StepLaunch L{};
+    L.g = h->grid;
+    L.N = h->N;
+    L.dt = (float)h->dt;
+    L.collision = h->cfg.collision;
+    L.lambda_iters = h->cfg.lambda_iters;
+    L.in = h->pop[h->cur];
+    L.out = h->pop[h->cur ^ 1];
+    L.ef_in = h->ef[h->cur];
+    L.ef_out = h->ef[h->cur ^ 1];
+    L.err = h->err;
+    L.budget_partials = nullptr;
+    int nblocks = 0;
+    if (h->cfg.budget) {
+      L.budget_partials = h->partials;
+      CK(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 2 * h->partials_cap, h->stream));
+    }
+    cudaError_t e = h->cfg.moving
+                        ? launch_step_moving(L, h->mc, h->table, h->cfg.storage, h->stream, &nblocks)
+                        : launch_step_static(L, h->sc, h->table, h->cfg.storage, h->stream, &nblocks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    ++launches;
+    if (h->nfrozen) {
+      e = launch_frozen(h->grid, h->N, h->nfrozen, h->frozen_cells, h->frozen_vals,
+                        h->pop[h->cur ^ 1], h->ef[h->cur ^ 1], h->cfg.storage, h->table,
+                        h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
+    }
+    if (h->cfg.budget) {
+      if (nblocks > h->partials_cap) return fail(h, LB_RT_ESTATE, "budget partials too small");
+      e = launch_budget_finalize(h->partials, nblocks, h->acc, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "budget kernel");
+    }
+    h->cur ^= 1;
+    ++h->steps;
+  }
+  if (h->timing) CK(h, cudaEventRecord(h->ev1, h->stream));
+  h->last_nlaunch = launches;
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_sync(lb_rt* h) {
+  if (!h) return LB_RT_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  unsigned word = 0;
+  CK(h, cudaMemcpy(&word, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (word) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "device error word 0x%08x", word);
+    return fail(h, LB_RT_ETIMEDOUT, buf);
+  }
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P, lb_rt_budget* budget,
+                           int ptr_kind) {
+  if (!h) return LB_RT_EINVAL;
+  if (ptr_kind != LB_RT_HOST && ptr_kind != LB_RT_DEVICE)
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
+  const long long S = h->grid.sites;
+  if (E || F || P) {
+    float *dE = E, *dF = F, *dP = P;
+    if (ptr_kind == LB_RT_HOST) {
+      if (!h->scratch) CK(h, cudaMalloc((void**)&h->scratch, sizeof(float) * 10 * S));
+      dE = E ? h->scratch : nullptr;
+      dF = F ? h->scratch + S : nullptr;
+      dP = P ? h->scratch + 4 * S : nullptr;
+    }
+    cudaError_t e = launch_moments(h->grid, h->N, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
+                                   h->table, dE, dF, dP, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    if (ptr_kind == LB_RT_HOST) {
+      if (E) CK(h, cudaMemcpyAsync(E, dE, sizeof(float) * S, cudaMemcpyDeviceToHost, h->stream));
+      if (F) CK(h, cudaMemcpyAsync(F, dF, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+      if (P) CK(h, cudaMemcpyAsync(P, dP, sizeof(float) * 6 * S, cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  if (budget) {
+    double a[8];
+    CK(h, cudaMemcpyAsync(a, h->acc, sizeof(a), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    budget->total = a[0];
+    budget->initial = a[1];
+    budget->outflow = a[2];
+    budget->source = a[3];
+    budget->injection = a[4];
+    budget->steps = (long long)a[5];
+  }
+  if (ptr_kind == LB_RT_HOST) return lb_rt_sync(h);
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
+  if (!h || !out) return fail(h, LB_RT_EINVAL, "null argument");
+  const size_t count = (size_t)h->grid.sites * h->N;
+  float* dst = out;
+  float* tmp = nullptr;
+  if (ptr_kind == LB_RT_HOST) {
+    CK(h, cudaMalloc((void**)&tmp, count * sizeof(float)));
+    dst = tmp;
+  } else if (ptr_kind != LB_RT_DEVICE) {
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
+  }
+  cudaError_t e = launch_decode(h->grid, h->N, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
+                                h->table, dst, h->stream);
+  if (e == cudaSuccess && tmp)
+    e = cudaMemcpyAsync(out, tmp, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_populations");
+  return ptr_kind == LB_RT_HOST ? lb_rt_sync(h) : LB_RT_OK;
+}
+
+size_t lb_rt_state_bytes(const lb_rt* h) {
+  if (!h) return 0;
+  size_t b = 64 + h->pop_bytes + 8 * sizeof(double);
+  if (h->ef[0]) b += sizeof(float4) * h->grid.sites;
+  return b;
+}
+
+lb_rt_status lb_rt_save_state(lb_rt* h, void* buf, size_t bytes) {
+  if (!h || !buf) return fail(h, LB_RT_EINVAL, "null argument");
+  if (bytes < lb_rt_state_bytes(h)) return fail(h, LB_RT_EINVAL, "buffer too small");
+  char* p = static_cast<char*>(buf);
+  long long hdr[8] = {0x4c42525453544154LL, h->N, h->grid.sites, h->cfg.storage, h->steps, 0, 0, 0};
+  std::memcpy(p, hdr, 64);
+  p += 64;
+  CK(h, cudaMemcpyAsync(p, h->pop[h->cur], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+  p += h->pop_bytes;
+  if (h->ef[0]) {
+    CK(h, cudaMemcpyAsync(p, h->ef[h->cur], sizeof(float4) * h->grid.sites, cudaMemcpyDeviceToHost,
+                          h->stream));
+    p += sizeof(float4) * h->grid.sites;
+  }
+  CK(h, cudaMemcpyAsync(p, h->acc, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return lb_rt_sync(h);
+}
+
+lb_rt_status lb_rt_restore_state(lb_rt* h, const void* buf, size_t bytes) {
+  if (!h || !buf) return fail(h, LB_RT_EINVAL, "null argument");
+  if (bytes < lb_rt_state_bytes(h)) return fail(h, LB_RT_EINVAL, "buffer too small");
+  const char* p = static_cast<const char*>(buf);
+  long long hdr[8];
+  std::memcpy(hdr, p, 64);
+  if (hdr[0] != 0x4c42525453544154LL || hdr[1] != h->N || hdr[2] != h->grid.sites ||
+      hdr[3] != h->cfg.storage)
+    return fail(h, LB_RT_EINVAL, "state does not match this handle");
+  p += 64;
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(h->pop[h->cur], p, h->pop_bytes, cudaMemcpyHostToDevice));
+  p += h->pop_bytes;
+  if (h->ef[0]) {
+    CK(h, cudaMemcpy(h->ef[h->cur], p, sizeof(float4) * h->grid.sites, cudaMemcpyHostToDevice));
+    p += sizeof(float4) * h->grid.sites;
+  }
+  CK(h, cudaMemcpy(h->acc, p, 8 * sizeof(double), cudaMemcpyHostToDevice));
+  h->steps = hdr[4];
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_directions(const lb_rt* h, int* ndir, double* dirs, double* weights,
+                              int8_t* signs) {
+  if (!h) return LB_RT_EINVAL;
+  if (ndir) *ndir = h->N;
+  for (int i = 0; i < h->N; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      if (dirs) dirs[3 * i + a] = h->n[3 * i + a];
+      if (signs) signs[3 * i + a] = h->n[3 * i + a] < 0.0 ? -1 : 1;
+    }
+    if (weights) weights[i] = h->w[i];
+  }
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_enable_timing(lb_rt* h, int on) {
+  if (!h) return LB_RT_EINVAL;
+  if (on && !h->ev0) {
+    CK(h, cudaEventCreate(&h->ev0));
+    CK(h, cudaEventCreate(&h->ev1));
+  }
+  h->timing = on != 0;
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch) {
+  if (!h) return LB_RT_EINVAL;
+  if (!h->timing) return fail(h, LB_RT_EINVAL, "timing not enabled");
+  CK(h, cudaEventSynchronize(h->ev1));
+  float t = 0.f;
+  CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
+  if (ms) *ms = t;
+  if (nlaunch) *nlaunch = h->last_nlaunch;
+  return LB_RT_OK;
+}
+
+}  // extern "C"
