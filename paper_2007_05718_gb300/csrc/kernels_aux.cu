@@ -1,6 +1,9 @@
-// Auxiliary kernels: initial populations, moments (Eqs. moments_discrete,
-// higher_moments), decoding to float32, frozen-cell overwrite and the FP64
-// energy-budget reductions.
+// Auxiliary kernels on the padded population layout: initial populations,
+// moments (Eqs. moments_discrete, higher_moments), decoding to dense
+// float32, frozen-cell overwrite and the FP64 energy-budget reductions.
+// Every population write also writes the site's periodic ghost mirrors.
+#include <algorithm>
+
 #include "lb_rt_internal.h"
 
 namespace lbrt {
@@ -9,39 +12,52 @@ namespace {
 
 constexpr int BLK = 256;
 
-__device__ __forceinline__ float load_pop(const void* pop, int storage, long long idx) {
-  (void)storage;
-  return static_cast<const float*>(pop)[idx];
+__device__ __forceinline__ void site_xyz(const Grid& g, long long s, int& x, int& y, int& z) {
+  x = (int)(s % g.nx);
+  const long long r = s / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
 }
 
+__device__ __forceinline__ float load_pop(const void* pop, const Grid& g, int i, int z, int y,
+                                          int x) {
+  return static_cast<const float*>(pop)[pidx(g, i, z, y, x)];
+}
+
+// kind: populations (data [N][sites]), isotropic (I_i = w_i E0) or P1
+// (I_i = w_i (E0 + d n_i.F0)).
 __global__ void k_init_state(Grid g, int N, const float* __restrict__ data, int kind,
                              float* __restrict__ pop, DirTable t) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= g.sites) return;
+  int x, y, z;
+  site_xyz(g, s, x, y, z);
   const float d = (float)g.dims;
-  if (kind == LB_RT_STATE_ISOTROPIC) {
-    const float E0 = data[s];
-    for (int i = 0; i < N; ++i) pop[(size_t)i * g.sites + s] = t.nw[i].w * E0;
-  } else {  // LB_RT_STATE_P1
-    const float E0 = data[s];
-    const float Fx = data[g.sites + s], Fy = data[2 * g.sites + s], Fz = data[3 * g.sites + s];
-    for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < N; ++i) {
+    float v;
+    if (kind == LB_RT_STATE_POPULATIONS) {
+      v = data[(size_t)i * g.sites + s];
+    } else if (kind == LB_RT_STATE_ISOTROPIC) {
+      v = t.nw[i].w * data[s];
+    } else {
       const float4 nw = t.nw[i];
-      pop[(size_t)i * g.sites + s] = nw.w * (E0 + d * (nw.x * Fx + nw.y * Fy + nw.z * Fz));
+      v = nw.w * (data[s] + d * (nw.x * data[g.sites + s] + nw.y * data[2 * g.sites + s] +
+                                 nw.z * data[3 * g.sites + s]));
     }
+    store_pop(pop, g, i, z, y, x, v);
   }
 }
 
-// E, F, P per site: plain sums over directions in float32 with per-site
-// accumulation in the direction order of the table.
-__global__ void k_moments(Grid g, int N, const void* __restrict__ pop, int storage,
-                          float* __restrict__ E, float* __restrict__ F, float* __restrict__ P,
-                          DirTable t) {
+// E, F, P per site: sums over directions in the table order.
+__global__ void k_moments(Grid g, int N, const void* __restrict__ pop, float* __restrict__ E,
+                          float* __restrict__ F, float* __restrict__ P, DirTable t) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= g.sites) return;
+  int x, y, z;
+  site_xyz(g, s, x, y, z);
   float e = 0, fx = 0, fy = 0, fz = 0, pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
   for (int i = 0; i < N; ++i) {
-    const float v = load_pop(pop, storage, (size_t)i * g.sites + s);
+    const float v = load_pop(pop, g, i, z, y, x);
     const float4 nw = t.nw[i];
     e += v;
     fx = fmaf(nw.x, v, fx);
@@ -70,12 +86,15 @@ __global__ void k_moments(Grid g, int N, const void* __restrict__ pop, int stora
   }
 }
 
-__global__ void k_decode(Grid g, int N, const void* __restrict__ pop, int storage,
-                         float* __restrict__ out) {
+__global__ void k_decode(Grid g, int N, const void* __restrict__ pop, float* __restrict__ out) {
   const long long total = g.sites * (long long)N;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x)
-    out[k] = load_pop(pop, storage, k);
+       k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k / g.sites);
+    int x, y, z;
+    site_xyz(g, k % g.sites, x, y, z);
+    out[k] = load_pop(pop, g, i, z, y, x);
+  }
 }
 
 // Frozen cells: overwrite, and add (prescribed - collided) energy to the
@@ -85,21 +104,20 @@ __global__ void k_frozen(Grid g, int N, int ncells, const int64_t* __restrict__ 
                          double* injection) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
-  const long long s = cells[c];
+  int x, y, z;
+  site_xyz(g, cells[c], x, y, z);
   double add = 0.0;
   for (int i = 0; i < N; ++i) {
-    const size_t k = (size_t)i * g.sites + s;
     const float v = vals[(size_t)c * N + i];
-    add += (double)v - (double)pop[k];
-    pop[k] = v;
+    add += (double)v - (double)pop[pidx(g, i, z, y, x)];
+    store_pop(pop, g, i, z, y, x, v);
   }
   if (injection) atomicAdd(injection, add);
 }
 
-// acc layout: [0] total, [1] initial, [2] outflow, [3] source, [4] injection, [5] steps.
+// acc layout: [0] total, [1] initial, [2] outflow, [3] source, [4] injection,
+// [5] steps, [6] injection of the current step (added by the frozen kernel).
 // partials: [nblocks][2] = (sum E*, sum E_collided) of the step just taken.
-// The frozen kernel of the same step adds its injection to acc[6]
-// (per-step scratch) before this finalisation folds it in.
 __global__ void k_budget_finalize(const double* __restrict__ partials, int nblocks, double* acc) {
   __shared__ double sa[BLK], sb[BLK];
   double a = 0.0, b = 0.0;
@@ -129,15 +147,17 @@ __global__ void k_budget_finalize(const double* __restrict__ partials, int nbloc
   }
 }
 
-// Total energy sum_sites sum_i I_i in FP64: per-block partials, then one block.
-__global__ void k_total_partials(Grid g, int N, const void* __restrict__ pop, int storage,
+// sum over sites of sum_i I_i in FP64: per-block partials, then one block.
+__global__ void k_total_partials(Grid g, int N, const void* __restrict__ pop,
                                  double* __restrict__ partials) {
   __shared__ double sh[BLK];
   double acc = 0.0;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.sites;
        s += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    site_xyz(g, s, x, y, z);
     float e = 0.f;
-    for (int i = 0; i < N; ++i) e += load_pop(pop, storage, (size_t)i * g.sites + s);
+    for (int i = 0; i < N; ++i) e += load_pop(pop, g, i, z, y, x);
     acc += (double)e;
   }
   sh[threadIdx.x] = acc;
@@ -167,38 +187,28 @@ unsigned grid1d(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 }  // namespace
 
 cudaError_t launch_init_state(const Grid& g, int N, const float* data, int kind, void* pop,
-                              float4* ef, int storage, const DirTable& t, cudaStream_t s) {
-  (void)ef;
+                              int storage, const DirTable& t, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  if (kind == LB_RT_STATE_POPULATIONS) {
-    return cudaMemcpyAsync(pop, data, sizeof(float) * g.sites * N, cudaMemcpyDeviceToDevice, s);
-  }
   k_init_state<<<grid1d(g.sites), BLK, 0, s>>>(g, N, data, kind, static_cast<float*>(pop), t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const Grid& g, int N, const void* pop, const float4* ef, int storage,
-                           const DirTable& t, float* E, float* F, float* P, cudaStream_t s) {
-  (void)ef;
+cudaError_t launch_moments(const Grid& g, int N, const void* pop, int storage, const DirTable& t,
+                           float* E, float* F, float* P, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  k_moments<<<grid1d(g.sites), BLK, 0, s>>>(g, N, pop, storage, E, F, P, t);
+  k_moments<<<grid1d(g.sites), BLK, 0, s>>>(g, N, pop, E, F, P, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_decode(const Grid& g, int N, const void* pop, const float4* ef, int storage,
-                          const DirTable& t, float* out, cudaStream_t s) {
-  (void)ef;
-  (void)t;
+cudaError_t launch_decode(const Grid& g, int N, const void* pop, int storage, float* out,
+                          cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  k_decode<<<1024, BLK, 0, s>>>(g, N, pop, storage, out);
+  k_decode<<<1024, BLK, 0, s>>>(g, N, pop, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_frozen(const Grid& g, int N, int ncells, const int64_t* cells, const float* vals,
-                          void* pop, float4* ef, int storage, const DirTable& t,
-                          double* injection_acc, cudaStream_t s) {
-  (void)ef;
-  (void)t;
+                          void* pop, int storage, double* injection_acc, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
   if (ncells <= 0) return cudaSuccess;
   k_frozen<<<(ncells + BLK - 1) / BLK, BLK, 0, s>>>(g, N, ncells, cells, vals,
@@ -212,15 +222,12 @@ cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, const float4* ef,
-                                int storage, const DirTable& t, double* partials, int max_blocks,
-                                double* out, cudaStream_t s) {
-  (void)ef;
-  (void)t;
+cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, int storage,
+                                double* partials, int max_blocks, double* out, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
   int nb = (int)std::min<long long>((long long)max_blocks, (long long)grid1d(g.sites));
   if (nb < 1) nb = 1;
-  k_total_partials<<<nb, BLK, 0, s>>>(g, N, pop, storage, partials);
+  k_total_partials<<<nb, BLK, 0, s>>>(g, N, pop, partials);
   k_sum_partials<<<1, BLK, 0, s>>>(partials, nb, out);
   return cudaGetLastError();
 }

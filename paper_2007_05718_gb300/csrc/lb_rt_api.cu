@@ -22,7 +22,9 @@ struct lb_rt {
   bool own_stream = false;
   int device = 0;
   void* pop[2] = {nullptr, nullptr};
-  float4* ef[2] = {nullptr, nullptr};
+  float4* ef[2] = {nullptr, nullptr};  // per-site moments of the reduced-precision modes
+  CUtensorMap tmap[2];                 // TMA descriptors of pop[0] / pop[1]
+  bool tmap_ok = false;
   int cur = 0;
   size_t pop_bytes = 0;
   // coefficient fields: static ka, k0, lam, eta (slots 0-3); moving v(3), kta, kt0, etat (4-7)
@@ -141,9 +143,8 @@ lb_rt_status copy_in(lb_rt* h, void* dst, const void* src, size_t bytes, int ptr
 
 lb_rt_status reset_budget(lb_rt* h) {
   CK(h, cudaMemsetAsync(h->acc, 0, 8 * sizeof(double), h->stream));
-  cudaError_t e = launch_total_energy(h->grid, h->N, h->pop[h->cur], h->ef[h->cur],
-                                      h->cfg.storage, h->table, h->partials, h->partials_cap,
-                                      h->acc, h->stream);
+  cudaError_t e = launch_total_energy(h->grid, h->N, h->pop[h->cur], h->cfg.storage,
+                                      h->partials, h->partials_cap, h->acc, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "total energy");
   CK(h, cudaMemcpyAsync(h->acc + 1, h->acc, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   return LB_RT_OK;
@@ -181,6 +182,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   if (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
       cfg->storage != LB_RT_BF16_DEV)
     return bad("bad storage");
+  if (cfg->storage != LB_RT_F32) return bad("reduced-precision storage is not available yet");
   if (cfg->collision != LB_RT_IMPLICIT_EXACT && cfg->collision != LB_RT_EXPLICIT &&
       cfg->collision != LB_RT_LAMBDA_K)
     return bad("bad collision");
@@ -205,6 +207,12 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   h->grid.dims = cfg->dims;
   h->grid.sites = sites;
   for (int a = 0; a < 3; ++a) h->grid.periodic[a] = cfg->bc[a] == LB_RT_PERIODIC;
+  // padded layout (see lb_rt_internal.h): rows of a multiple of 8 elements
+  h->grid.PX = ((cfg->nx + GL + 1) + 7) / 8 * 8;
+  h->grid.PY = cfg->ny + 2;
+  h->grid.PZ = cfg->nz + 2;
+  h->grid.plane = (long long)h->grid.PX * h->grid.PY;
+  h->grid.dstride = h->grid.plane * h->grid.PZ;
   h->dt = cfg->cfl * cfg->dx;
   fill_table(h);
 
@@ -220,7 +228,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     h->own_stream = (e == cudaSuccess);
   }
-  h->pop_bytes = (size_t)sites * h->N * elem_bytes(cfg->storage);
+  h->pop_bytes = (size_t)h->grid.dstride * h->N * elem_bytes(cfg->storage);
   const int max_blocks = 4096;
   auto alloc = [&](void** p, size_t b) {
     if (e != cudaSuccess) return;
@@ -232,9 +240,9 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     alloc((void**)&h->ef[0], sizeof(float4) * sites);
     alloc((void**)&h->ef[1], sizeof(float4) * sites);
   }
-  // budget partials: one slot pair per CTA of the step kernel (grid of
-  // ceil(nx/32) x ceil(ny/4) x nz), at least max_blocks for the reductions
-  const long long step_blocks = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 3) / 4) * cfg->nz;
+  // budget partials: one slot pair per CTA of the step kernel; every step
+  // kernel's grid is at most ceil(nx/32) x ny x nz CTAs
+  const long long step_blocks = (long long)((cfg->nx + 31) / 32) * cfg->ny * cfg->nz;
   h->partials_cap = (int)std::max<long long>(max_blocks, step_blocks);
   alloc((void**)&h->partials, sizeof(double) * 2 * h->partials_cap);
   alloc((void**)&h->acc, sizeof(double) * 8);
@@ -246,7 +254,9 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   }
   h->sc = StaticCoef{nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f};
   h->mc = MovingCoef{nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, 0.f};
+  // zero both buffers: ghost cells of vacuum faces stay zero for good
   e = cudaMemsetAsync(h->pop[0], 0, h->pop_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, h->pop_bytes, h->stream);
   if (e == cudaSuccess && h->ef[0]) e = cudaMemsetAsync(h->ef[0], 0, sizeof(float4) * sites, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
@@ -255,6 +265,18 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     g_create_msg = std::string("init: ") + cudaGetErrorString(e);
     lb_rt_destroy(h);
     return LB_RT_ECUDA;
+  }
+  if (cfg->storage == LB_RT_F32 && !cfg->moving) {
+    std::string terr;
+    const int zc = tma_planes_per_batch(h->N);
+    for (int b = 0; b < 2; ++b) {
+      if (!make_pop_tensor_map(&h->tmap[b], h->grid, h->N, h->pop[b], zc, terr)) {
+        g_create_msg = terr;
+        lb_rt_destroy(h);
+        return LB_RT_ECUDA;
+      }
+    }
+    h->tmap_ok = true;
   }
   *out = h;
   return LB_RT_OK;
@@ -345,8 +367,8 @@ lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind
     return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   }
   h->cur = 0;
-  cudaError_t e = launch_init_state(h->grid, h->N, src, kind, h->pop[0], h->ef[0],
-                                    h->cfg.storage, h->table, h->stream);
+  cudaError_t e = launch_init_state(h->grid, h->N, src, kind, h->pop[0], h->cfg.storage,
+                                    h->table, h->stream);
   if (tmp) {
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
@@ -394,10 +416,10 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     L.lambda_iters = h->cfg.lambda_iters;
     L.in = h->pop[h->cur];
     L.out = h->pop[h->cur ^ 1];
-    L.ef_in = h->ef[h->cur];
-    L.ef_out = h->ef[h->cur ^ 1];
+    L.tmap_in = h->tmap_ok ? &h->tmap[h->cur] : nullptr;
     L.err = h->err;
     L.budget_partials = nullptr;
+    L.partials_cap = h->partials_cap;
     int nblocks = 0;
     if (h->cfg.budget) {
       L.budget_partials = h->partials;
@@ -410,12 +432,11 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     ++launches;
     if (h->nfrozen) {
       e = launch_frozen(h->grid, h->N, h->nfrozen, h->frozen_cells, h->frozen_vals,
-                        h->pop[h->cur ^ 1], h->ef[h->cur ^ 1], h->cfg.storage, h->table,
+                        h->pop[h->cur ^ 1], h->cfg.storage,
                         h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
     }
     if (h->cfg.budget) {
-      if (nblocks > h->partials_cap) return fail(h, LB_RT_ESTATE, "budget partials too small");
       e = launch_budget_finalize(h->partials, nblocks, h->acc, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "budget kernel");
     }
@@ -454,7 +475,7 @@ lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P, lb_rt_budget*
       dF = F ? h->scratch + S : nullptr;
       dP = P ? h->scratch + 4 * S : nullptr;
     }
-    cudaError_t e = launch_moments(h->grid, h->N, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
+    cudaError_t e = launch_moments(h->grid, h->N, h->pop[h->cur], h->cfg.storage,
                                    h->table, dE, dF, dP, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     if (ptr_kind == LB_RT_HOST) {
@@ -489,8 +510,7 @@ lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
   } else if (ptr_kind != LB_RT_DEVICE) {
     return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   }
-  cudaError_t e = launch_decode(h->grid, h->N, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
-                                h->table, dst, h->stream);
+  cudaError_t e = launch_decode(h->grid, h->N, h->pop[h->cur], h->cfg.storage, dst, h->stream);
   if (e == cudaSuccess && tmp)
     e = cudaMemcpyAsync(out, tmp, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(h->stream);

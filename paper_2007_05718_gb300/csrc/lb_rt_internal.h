@@ -2,6 +2,7 @@
 // liblbrt.so.  Nothing here is part of the public ABI (include/lb_rt.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -14,26 +15,45 @@
 
 namespace lbrt {
 
-// Per-direction constants handed to the step kernels by value (kernel
-// parameters live in the constant bank, so a warp reading the same
-// direction gets a broadcast).  nw = (n_x, n_y, n_z, w);
-// au = (a_x, a_y, a_z, upwind octant bits) with a = cfl |n| the weight of
-// the upwind corner along each axis in Eq. (interp); octant bit k set means
-// sgn(n_k) = -1, i.e. the pull reads the +1 neighbour along axis k.
+// Per-direction constants handed to the kernels by value (kernel parameters
+// live in the constant bank, so a warp reading the same direction gets a
+// broadcast).  nw = (n_x, n_y, n_z, w); au = (a_x, a_y, a_z, octant bits),
+// a = cfl |n| the weight of the upwind corner along each axis in Eq. (interp);
+// octant bit k set means sgn(n_k) = -1, i.e. the pull reads the +1 neighbour
+// along axis k.
 struct DirTable {
   float4 nw[LB_RT_MAX_DIRS];
   float4 au[LB_RT_MAX_DIRS];
 };
 
-// Geometry and boundary data of one grid.
+// Device layout of a population buffer.  Every direction holds a padded
+// block [PZ][PY][PX] with one ghost layer around the nz x ny x nx interior:
+// site (x, y, z) lives at column x + GL, row y + 1, plane z + 1.  GL = 2
+// keeps even x at even columns (8-byte pairs); PX is rounded up so that rows
+// start on 16-byte boundaries (TMA strides) in every storage type.  Ghost
+// cells of a periodic axis mirror the opposite interior edge (column 1 <-
+// x = nx - 1, column nx + GL <- x = 0, row 0 <- y = ny - 1, row ny + 1 <- y = 0,
+// plane 0 <- z = nz - 1, plane nz + 1 <- z = 0); on a vacuum axis they stay 0.
+// Every kernel that writes populations also writes the mirrors, so a pull
+// from x - 1, y - 1 or z - 1 (or + 1) never needs boundary logic.
+constexpr int GL = 2;
+
 struct Grid {
   int nx, ny, nz;
   int dims;
   long long sites;   // nx * ny * nz
   int periodic[3];   // per axis x, y, z
+  int PX, PY, PZ;    // padded extents
+  long long plane;   // PX * PY
+  long long dstride; // PX * PY * PZ: elements per direction
 };
 
-// Site coefficient fields: pointer == nullptr means "use the scalar".
+__host__ __device__ inline long long pidx(const Grid& g, int i, int z, int y, int x) {
+  return (long long)i * g.dstride + (long long)(z + 1) * g.plane + (long long)(y + 1) * g.PX +
+         (x + GL);
+}
+
+// Site coefficient fields (dense [nz][ny][nx]): nullptr means "use the scalar".
 struct StaticCoef {
   const float* ka; const float* k0; const float* lam; const float* eta;
   float ka_s, k0_s, lam_s, eta_s;
@@ -53,36 +73,78 @@ struct StepLaunch {
   float dt;
   int collision;       // LB_RT_IMPLICIT_EXACT / LB_RT_EXPLICIT / LB_RT_LAMBDA_K
   int lambda_iters;
-  const void* in;      // populations at t
+  const void* in;      // populations at t (padded layout)
   void* out;           // populations at t + dt
-  const float4* ef_in; // per-site moments of `in` (reduced-precision modes)
-  float4* ef_out;
+  const CUtensorMap* tmap_in;  // TMA descriptor of `in` (host copy)
   double* budget_partials;  // [nblocks][2] (sum E*, sum E_collided) or nullptr
+  long long partials_cap;   // slots available; a launcher whose grid is larger refuses
   unsigned* err;            // device error word
 };
 
-// Kernel launchers (kernels_*.cu).  Return cudaGetLastError().
+// Kernel launchers.  Return cudaGetLastError() (or an error without
+// launching when the configuration is not supported).
 cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks);
 cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks);
-cudaError_t launch_moments(const Grid& g, int N, const void* pop, const float4* ef, int storage,
+cudaError_t launch_moments(const Grid& g, int N, const void* pop, int storage,
                            const DirTable& t, float* E, float* F, float* P, cudaStream_t s);
 cudaError_t launch_init_state(const Grid& g, int N, const float* data, int kind, void* pop,
-                              float4* ef, int storage, const DirTable& t, cudaStream_t s);
-cudaError_t launch_decode(const Grid& g, int N, const void* pop, const float4* ef, int storage,
-                          const DirTable& t, float* out, cudaStream_t s);
+                              int storage, const DirTable& t, cudaStream_t s);
+cudaError_t launch_decode(const Grid& g, int N, const void* pop, int storage, float* out,
+                          cudaStream_t s);
 cudaError_t launch_frozen(const Grid& g, int N, int ncells, const int64_t* cells, const float* vals,
-                          void* pop, float4* ef, int storage, const DirTable& t,
-                          double* injection_acc, cudaStream_t s);
+                          void* pop, int storage, double* injection_acc, cudaStream_t s);
 cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* acc,
                                    cudaStream_t s);
-cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, const float4* ef,
-                                int storage, const DirTable& t, double* partials, int max_blocks,
-                                double* out, cudaStream_t s);
+cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, int storage,
+                                double* partials, int max_blocks, double* out, cudaStream_t s);
+
+// TMA descriptor of a padded float32 population buffer viewed as the 3D
+// tensor [N * PZ][PY][PX] with box (68, 2, zc) (kernels_tma.cu).
+bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int N, void* base, int zc,
+                         std::string& err);
+int tma_planes_per_batch(int N);
 
 // Direction sets built on the host (directions.cpp).
 bool build_directions(const lb_rt_config& cfg, std::vector<double>& n, std::vector<double>& w,
                       std::string& err);
+
+// ---- device helpers shared by the kernels --------------------------------
+
+// Padded positions mirroring interior coordinate c of an axis of extent n:
+// the own position and, on a periodic axis, the ghost on the opposite side.
+__device__ __forceinline__ int mirrors(int c, int n, int periodic, int off, int* out) {
+  int m = 0;
+  out[m++] = c + off;
+  if (periodic) {
+    if (c == n - 1) out[m++] = off - 1;
+    if (c == 0) out[m++] = n + off;
+  }
+  return m;
+}
+
+// Store one population value at site (x, y, z) of direction i and at every
+// ghost mirror of that site on the periodic axes.
+template <class T>
+__device__ __forceinline__ void store_pop(T* pop, const Grid& g, int i, int z, int y, int x,
+                                          T v) {
+  int xs[3], ys[3], zs[3];
+  const int nxs = mirrors(x, g.nx, g.periodic[0], GL, xs);
+  const int nys = mirrors(y, g.ny, g.periodic[1], 1, ys);
+  const int nzs = mirrors(z, g.nz, g.periodic[2], 1, zs);
+  const long long base = (long long)i * g.dstride;
+  for (int a = 0; a < nzs; ++a)
+    for (int b = 0; b < nys; ++b)
+      for (int c = 0; c < nxs; ++c)
+        pop[base + (long long)zs[a] * g.plane + (long long)ys[b] * g.PX + xs[c]] = v;
+}
+
+// True when site (x, y, z) has at least one ghost mirror.
+__device__ __forceinline__ bool has_mirror(const Grid& g, int z, int y, int x) {
+  return (g.periodic[0] && (x == 0 || x == g.nx - 1)) ||
+         (g.periodic[1] && (y == 0 || y == g.ny - 1)) ||
+         (g.periodic[2] && (z == 0 || z == g.nz - 1));
+}
 
 }  // namespace lbrt

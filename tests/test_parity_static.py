@@ -230,3 +230,20 @@ def test_invalid_calls_return_errors(cuda):
             lbrt.lb_rt_restore_state(h, b"\0" * 16)
     finally:
         lbrt.lb_rt_destroy(h)
+
+
+@pytest.mark.parametrize("nx", [36, 38, 37, 8, 4])
+@pytest.mark.parametrize("bc", ["ppp", "vvv"])
+def test_kernel_paths_by_row_width(cuda, nx, bc):
+    """Row widths that select each step kernel: multiples of 4 (bulk-copy
+    kernel), even (paired kernel), odd (scalar z-marching kernel); windows
+    narrower than the 72-column tile wrap several times."""
+    shape = (19, 5, nx)
+    coef = dict(kappa_a=W.random_fields(shape, 51, 0.0, 10.0), kappa_0=W.random_fields(shape, 52, 0.0, 40.0),
+                lam=0.3, eta=W.random_fields(shape, 53, 0.0, 2.0))
+    p = Problem(3, shape, "ico", level=1, bc=bc, coef=coef,
+                state=W.random_populations(42, shape, 54), budget=True)
+    _check(p, 5, f_scale="E")
+    p2 = Problem(3, shape, "ico", level=2, bc=bc, coef=coef,
+                 state=W.random_populations(162, shape, 55))
+    _check(p2, 3, f_scale="E")
