@@ -24,23 +24,28 @@ __device__ __forceinline__ float load_pop(const void* pop, const Grid& g, int i,
   return static_cast<const float*>(pop)[pidx(g, i, z, y, x)];
 }
 
-// kind: populations (data [N][sites]), isotropic (I_i = w_i E0) or P1
-// (I_i = w_i (E0 + d n_i.F0)).
-__global__ void k_init_state(Grid g, int N, const float* __restrict__ data, int kind,
-                             float* __restrict__ pop, DirTable t) {
+// kind: populations (data [Next][sites] in the external order), isotropic
+// (I_i = w_i E0) or P1 (I_i = w_i (E0 + d n_i.F0)).  Inert padding directions
+// (w = 0, n = 0) get 0.
+__global__ void k_init_state(Grid g, int Ni, int Next, const int* __restrict__ int_of_ext,
+                             const float* __restrict__ data, int kind, float* __restrict__ pop,
+                             DirTable t) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= g.sites) return;
   int x, y, z;
   site_xyz(g, s, x, y, z);
   const float d = (float)g.dims;
-  for (int i = 0; i < N; ++i) {
+  if (kind == LB_RT_STATE_POPULATIONS) {
+    for (int e = 0; e < Next; ++e)
+      store_pop(pop, g, int_of_ext[e], z, y, x, data[(size_t)e * g.sites + s]);
+    return;
+  }
+  for (int i = 0; i < Ni; ++i) {
+    const float4 nw = t.nw[i];
     float v;
-    if (kind == LB_RT_STATE_POPULATIONS) {
-      v = data[(size_t)i * g.sites + s];
-    } else if (kind == LB_RT_STATE_ISOTROPIC) {
-      v = t.nw[i].w * data[s];
+    if (kind == LB_RT_STATE_ISOTROPIC) {
+      v = nw.w * data[s];
     } else {
-      const float4 nw = t.nw[i];
       v = nw.w * (data[s] + d * (nw.x * data[g.sites + s] + nw.y * data[2 * g.sites + s] +
                                  nw.z * data[3 * g.sites + s]));
     }
@@ -86,29 +91,32 @@ __global__ void k_moments(Grid g, int N, const void* __restrict__ pop, float* __
   }
 }
 
-__global__ void k_decode(Grid g, int N, const void* __restrict__ pop, float* __restrict__ out) {
-  const long long total = g.sites * (long long)N;
+// Dense [Next][sites] float32 copy in the external direction order.
+__global__ void k_decode(Grid g, int Next, const int* __restrict__ int_of_ext,
+                         const void* __restrict__ pop, float* __restrict__ out) {
+  const long long total = g.sites * (long long)Next;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(k / g.sites);
+    const int e = (int)(k / g.sites);
     int x, y, z;
     site_xyz(g, k % g.sites, x, y, z);
-    out[k] = load_pop(pop, g, i, z, y, x);
+    out[k] = load_pop(pop, g, int_of_ext[e], z, y, x);
   }
 }
 
 // Frozen cells: overwrite, and add (prescribed - collided) energy to the
 // FP64 injection accumulator.
-__global__ void k_frozen(Grid g, int N, int ncells, const int64_t* __restrict__ cells,
-                         const float* __restrict__ vals, float* __restrict__ pop,
-                         double* injection) {
+__global__ void k_frozen(Grid g, int Next, const int* __restrict__ int_of_ext, int ncells,
+                         const int64_t* __restrict__ cells, const float* __restrict__ vals,
+                         float* __restrict__ pop, double* injection) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
   int x, y, z;
   site_xyz(g, cells[c], x, y, z);
   double add = 0.0;
-  for (int i = 0; i < N; ++i) {
-    const float v = vals[(size_t)c * N + i];
+  for (int e = 0; e < Next; ++e) {
+    const int i = int_of_ext[e];
+    const float v = vals[(size_t)c * Next + e];
     add += (double)v - (double)pop[pidx(g, i, z, y, x)];
     store_pop(pop, g, i, z, y, x, v);
   }
@@ -186,10 +194,12 @@ unsigned grid1d(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 
 }  // namespace
 
-cudaError_t launch_init_state(const Grid& g, int N, const float* data, int kind, void* pop,
-                              int storage, const DirTable& t, cudaStream_t s) {
+cudaError_t launch_init_state(const Grid& g, int Ni, int Next, const int* int_of_ext,
+                              const float* data, int kind, void* pop, int storage,
+                              const DirTable& t, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  k_init_state<<<grid1d(g.sites), BLK, 0, s>>>(g, N, data, kind, static_cast<float*>(pop), t);
+  k_init_state<<<grid1d(g.sites), BLK, 0, s>>>(g, Ni, Next, int_of_ext, data, kind,
+                                               static_cast<float*>(pop), t);
   return cudaGetLastError();
 }
 
@@ -200,18 +210,19 @@ cudaError_t launch_moments(const Grid& g, int N, const void* pop, int storage, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_decode(const Grid& g, int N, const void* pop, int storage, float* out,
-                          cudaStream_t s) {
+cudaError_t launch_decode(const Grid& g, int Next, const int* int_of_ext, const void* pop,
+                          int storage, float* out, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  k_decode<<<1024, BLK, 0, s>>>(g, N, pop, out);
+  k_decode<<<1024, BLK, 0, s>>>(g, Next, int_of_ext, pop, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_frozen(const Grid& g, int N, int ncells, const int64_t* cells, const float* vals,
-                          void* pop, int storage, double* injection_acc, cudaStream_t s) {
+cudaError_t launch_frozen(const Grid& g, int Next, const int* int_of_ext, int ncells,
+                          const int64_t* cells, const float* vals, void* pop, int storage,
+                          double* injection_acc, cudaStream_t s) {
   if (storage != ST_F32) return cudaErrorNotSupported;
   if (ncells <= 0) return cudaSuccess;
-  k_frozen<<<(ncells + BLK - 1) / BLK, BLK, 0, s>>>(g, N, ncells, cells, vals,
+  k_frozen<<<(ncells + BLK - 1) / BLK, BLK, 0, s>>>(g, Next, int_of_ext, ncells, cells, vals,
                                                     static_cast<float*>(pop), injection_acc);
   return cudaGetLastError();
 }

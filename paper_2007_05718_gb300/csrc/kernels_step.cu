@@ -15,7 +15,7 @@
 namespace lbrt {
 
 cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
-                              cudaStream_t s, int* nblocks);
+                              int dpt, int zc, cudaStream_t s, int* nblocks);
 
 namespace {
 
@@ -27,8 +27,8 @@ constexpr int TY = 4;  // sites per CTA along y (32 along x)
 __device__ __forceinline__ float pull(const float* __restrict__ p, const Grid& g, float4 au) {
   const int oct = __float_as_int(au.w);
   const long long dxo = (oct & 1) ? 1 : -1;
-  const long long dyo = (oct & 2) ? g.PX : -(long long)g.PX;
-  const long long dzo = (oct & 4) ? g.plane : -g.plane;
+  const long long dyo = (oct & 2) ? g.sy : -g.sy;
+  const long long dzo = (oct & 4) ? g.sz : -g.sz;
   const float ax = au.x, ay = au.y, az = au.z;
   const float v000 = __ldg(p);
   const float v100 = __ldg(p + dxo);
@@ -174,7 +174,7 @@ cudaError_t launch_moving(const StepLaunch& L, const MovingCoef& c, const DirTab
 cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks) {
   if (storage != ST_F32) return cudaErrorNotSupported;
-  return launch_tma_static(L, c, t, s, nblocks);
+  return launch_tma_static(L, c, t, L.dpt, L.zc, s, nblocks);
 }
 
 cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,

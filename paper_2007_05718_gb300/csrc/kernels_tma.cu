@@ -3,27 +3,32 @@
 // (rte_implicit), (collision-step).
 //
 // Work decomposition.  A CTA owns 64 consecutive x sites of one row y and a
-// chunk of planes in z; each lane owns an x-pair (2 sites, packed f32x2
-// arithmetic).  The G warps split the N directions (DPT each) and the chunk
-// is processed in batches of ZC planes.
+// chunk of planes in z; each lane owns an x-pair (2 sites, packed FFMA2
+// arithmetic).  Warp g owns the DPT directions g DPT .. g DPT + DPT - 1 of the
+// library's internal direction order, in which directions are grouped by
+// (sgn n^y, sgn n^z) and every group is padded to a multiple of DPT with inert
+// zero-weight directions; so all directions of a warp pull from the same
+// upwind row and plane.  The chunk is processed in batches of ZC planes.
 //
-// Data movement.  For every (direction, batch) item a warp needs, per plane,
-// the own row y and the upwind row y - sgn(n^y) over the columns
-// x0 - 2 .. x0 + 65.  In the padded population layout these are one box of
-// 68 x 2 x ZC floats (the ghost layer supplies periodic images and vacuum
-// zeros), fetched by a single cp.async.bulk.tensor.3d issued by lane 0 with
-// completion counted on an mbarrier.  Each warp keeps a ring of R slots and
-// fetches R - 1 items ahead, so later directions (and the next batch,
-// across the CTA barriers) are in flight while the current one is computed.
-// Waits are bounded: a wait that gives up sets the device error word and the
-// CTA runs to its end without further compute.
+// Data movement.  Per batch a warp needs, for each of its directions and
+// each of the ZC planes, the own row y and the upwind row y - sgn(n^y) over
+// the columns x0 - 2 .. x0 + 65.  In the padded layout [z][y][dir][x] these
+// form ONE box of 68 x DPT x 2 x ZC floats (the ghost layer supplies
+// periodic images and vacuum zeros), fetched by a single TMA load issued by
+// lane 0; large boxes keep the copy engine near full bandwidth.  Each warp
+// double-buffers its boxes (the next batch is in flight while the current
+// one is computed).  Waits are bounded: a wait that gives up sets the device
+// error word and the CTA runs to its end without further compute.
 //
-// Arithmetic per item and plane: the bilinear value of the two rows (x then
-// y), a lerp in z against the plane carried in a register from the previous
-// plane (Eq. interp factorised), I* staged in shared memory and the partial
-// (E*, F*) accumulated; after the batch the G partials give the site
-// scalars of the collision and I_i^{n+1} = alpha I*_i + w_i (c0 + n_i . c1) is
-// stored as float2 (plus ghost mirrors at periodic faces).
+// Arithmetic per direction and plane: the bilinear value of the two rows
+// (x then y), a lerp in z against the plane carried in a register from the
+// previous plane (Eq. interp factorised), I* kept in registers and the
+// partial (E*, F*) accumulated; after the batch, one CTA barrier exchanges
+// the G partial moments, every warp forms the collision scalars of its own
+// lanes' sites, and I_i^{n+1} = alpha I*_i + w_i (c0 + n_i . c1) is stored as
+// float2 (plus ghost mirrors at periodic faces).
+#include <algorithm>
+
 #include "lb_rt_internal.h"
 
 #include <cudaTypedefs.h>
@@ -32,41 +37,14 @@ namespace lbrt {
 
 namespace {
 
-// ---- packed float32 x 2 arithmetic --------------------------------------
-__device__ __forceinline__ unsigned long long pk2(float2 a) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
-  return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long r) {
-  float2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
-  return a;
-}
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
-}
+// ---- packed float32 x 2 arithmetic (FFMA2 / FADD2 / FMUL2 builtins) -------
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
-// weight t on a, 1 - t on b
-__device__ __forceinline__ float2 f2lerp(float2 t, float2 a, float2 b) {
-  return f2fma(t, f2sub(a, b), b);
+// t a + (1 - t) b as two fused multiply-adds, with nt = -t precomputed
+__device__ __forceinline__ float2 f2lerp(float2 t, float2 nt, float2 a, float2 b) {
+  return __ffma2_rn(t, a, __ffma2_rn(nt, b, b));
 }
 
 // ---- mbarrier and TMA ------------------------------------------------------
@@ -90,20 +68,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint32_t bar) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-constexpr int BOXX = 68;                       // columns x0 - 2 .. x0 + 65
-constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: longer is a fault
+constexpr int BOXX = 68;                          // columns x0 - 2 .. x0 + 65
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: longer is a fault
 
 // Bounded wait on an mbarrier phase.  Returns false (and sets the error
 // word) when the phase has not completed within WAIT_CYCLES SM cycles.
@@ -180,33 +158,43 @@ __device__ __forceinline__ Coef collide_scalars(int mode, int iters, float dt, f
   return c;
 }
 
-template <int ZC>
+template <int DPT, int ZC>
 __host__ __device__ constexpr int slot_floats() {
-  return ((BOXX * 2 * ZC * 4 + 127) / 128) * 32;  // 128-byte aligned slots
+  return ((BOXX * DPT * 2 * ZC * 4 + 127) / 128) * 32;  // 128-byte aligned slots
 }
 
-template <int DPT, int ZC, int R>
-__global__ void __launch_bounds__(256)
-k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const StaticCoef cf,
-             const DirTable t, int zchunk) {
+// In-plane bilinear value of the lane's pair from one box row pair: r0 the
+// own row, r1 the upwind row (pointers at the window column of the pair),
+// upwind column at offset `du` (-1 or +2) from the pair's first site.
+__device__ __forceinline__ float2 bilinear(const float* r0, const float* r1, int du, bool xneg,
+                                           float2 ax, float2 nax, float2 ay, float2 nay) {
+  const float2 v0 = *reinterpret_cast<const float2*>(r0);
+  const float2 v1 = *reinterpret_cast<const float2*>(r1);
+  const float u0 = r0[du], u1 = r1[du];
+  const float2 w0 = xneg ? make_float2(v0.y, u0) : make_float2(u0, v0.x);
+  const float2 w1 = xneg ? make_float2(v1.y, u1) : make_float2(u1, v1.x);
+  return f2lerp(ay, nay, f2lerp(ax, nax, w1, v1), f2lerp(ax, nax, w0, v0));
+}
+
+template <int DPT, int ZC, int R, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const StaticCoef cf,
+           const DirTable t, int zchunk) {
+  constexpr int SLOT = slot_floats<DPT, ZC>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr int SLOT = slot_floats<ZC>();
   const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
   const Grid& gr = L.g;
-  const int nx = gr.nx, nz = gr.nz;
-  const int NP = G * DPT;
-  // shared layout: ring [G][R][SLOT] | I* [NP][ZC][32] float2 | part [G][ZC][4][32] float2 |
-  //                coef [ZC][5][32] float2 | mbar [G][R] | abort flag
+  const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+  // shared layout: ring [G][R][SLOT] | part [2][G][ZC][4][32] float2 | mbar [G][R] | abort flag
   float* ring = reinterpret_cast<float*>(smem_raw);
-  float2* Ist = reinterpret_cast<float2*>(ring + (size_t)G * R * SLOT);
-  float2* part = Ist + (size_t)NP * ZC * 32;
-  float2* coef = part + (size_t)G * ZC * 4 * 32;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(coef + (size_t)ZC * 5 * 32);
-  int* abort_flag = reinterpret_cast<int*>(mbar + G * R);
+  float2* part2 = reinterpret_cast<float2*>(ring + (size_t)G * R * SLOT);
+  unsigned long long* mbar =
+      reinterpret_cast<unsigned long long*>(part2 + (size_t)2 * G * ZC * 4 * 32);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mbar + G * R);
 
   const int x0 = blockIdx.x * 64;
-  const int xa = x0 + 2 * lane;       // the lane's pair (xa, xa + 1)
+  const int xa = x0 + 2 * lane;  // the lane's pair (xa, xa + 1)
   const bool in0 = xa < nx, in1 = xa + 1 < nx;
   const int y = blockIdx.y;
   const int zbeg = blockIdx.z * zchunk;
@@ -214,7 +202,12 @@ k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const
   const float inv_d = 1.f / (float)gr.dims;
   float* __restrict__ out = static_cast<float*>(L.out);
   const int nbatch = (zend - zbeg + ZC - 1) / ZC;
-  const int nitems = (nbatch + 1) * DPT;  // item q: batch q / DPT - 1 (-1: prologue), dir q % DPT
+  const int i0 = g * DPT;
+  // the warp's row / plane class (uniform over its directions)
+  const int oct0 = __float_as_int(t.au[i0].w);
+  const bool yneg = oct0 & 2;
+  const int zs = (oct0 & 4) ? 1 : 0;
+  const int row_own = yneg ? 0 : 1, row_up = yneg ? 1 : 0;
 
   if (lane == 0) {
     for (int r = 0; r < R; ++r) mbar_init(smem_u32(&mbar[g * R + r]), 1);
@@ -226,118 +219,114 @@ k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const
   float* my_ring = ring + (size_t)g * R * SLOT;
   bool alive = true;
   int issued = 0;
-  // issue item q into slot q % R (lane 0)
+  // item q = batch q - 1 (q = 0: the plane below the chunk, for the carries)
   auto issue = [&](int q) {
-    if (q >= nitems || !alive) return;
+    if (q > nbatch || !alive) return;
     issued = q + 1;
     __syncwarp();
     if (lane == 0) {
       const int slot = q % R;
       const uint32_t bar = smem_u32(&mbar[g * R + slot]);
-      const int i = g * DPT + (q % DPT);
-      if (i < L.N) {
-        fence_proxy_async();
-        const int oct = __float_as_int(t.au[i].w);
-        const int s = (oct & 4) ? 1 : 0;
-        const int b = q / DPT - 1;
-        // first plane of the box (padded coordinates: plane z + 1)
-        const int zp = (b < 0 ? zbeg - 1 : zbeg + b * ZC) + s + 1;
-        const int yp = (oct & 2) ? y + 1 : y;  // lower of the two rows (padded)
-        mbar_arrive_tx(bar, BOXX * 2 * ZC * 4);
-        tma_load_3d(smem_u32(my_ring + (size_t)slot * SLOT), &tmap, x0,
-                    yp, i * gr.PZ + zp, bar);
-      } else {
-        mbar_arrive_tx(bar, 0);
-      }
+      const int zp = (q == 0 ? zbeg - 1 : zbeg + (q - 1) * ZC) + zs + 1;  // padded plane
+      const int yp = yneg ? y + 1 : y;                                 // lower row (padded)
+      fence_proxy_async();
+      mbar_arrive_tx(bar, BOXX * DPT * 2 * ZC * 4);
+      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOT), &tmap, x0, i0, yp, zp, bar);
     }
   };
   auto wait_item = [&](int q) -> bool {
-    if (!alive || *reinterpret_cast<volatile int*>(abort_flag)) {
+    if (!alive || *abort_flag) {
       alive = false;
       return false;
     }
     if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), (uint32_t)((q / R) & 1), L.err)) {
-      *reinterpret_cast<volatile int*>(abort_flag) = 1;
+      *abort_flag = 1;
       alive = false;
       return false;
     }
     return true;
   };
+  // element (plane j, row r, direction k) of a slot, at the lane's pair
+  const int wc = 2 + 2 * lane;  // window column of xa: x - (x0 - 2)
+  auto at = [&](const float* slot, int j, int r, int k) {
+    return slot + ((j * 2 + r) * DPT + k) * BOXX + wc;
+  };
 
-  int q = 0;
   for (int r = 0; r < R - 1; ++r) issue(r);
 
-  // window column of the lane's pair: x - (x0 - 2)
-  const int wc = 2 + 2 * lane;
   float2 carry[DPT];
+  {
+    issue(R - 1);
+    const bool ok = wait_item(0);
+    const float* slot = my_ring;
 #pragma unroll
-  for (int k = 0; k < DPT; ++k) {
-    issue(q + R - 1);
-    carry[k] = make_float2(0.f, 0.f);
-    const int i = g * DPT + k;
-    if (wait_item(q) && i < L.N) {
-      const float4 au = t.au[i];
-      const int oct = __float_as_int(au.w);
-      const bool xneg = oct & 1;
-      const float* slot = my_ring + (size_t)(q % R) * SLOT;
-      const float* r0 = slot + ((oct & 2) ? 0 : BOXX);   // own row
-      const float* r1 = slot + ((oct & 2) ? BOXX : 0);   // upwind row
-      const int uc = xneg ? wc + 2 : wc - 1;
-      const float2 v0 = *reinterpret_cast<const float2*>(r0 + wc);
-      const float2 v1 = *reinterpret_cast<const float2*>(r1 + wc);
-      const float u0 = r0[uc], u1 = r1[uc];
-      const float2 w0 = xneg ? make_float2(v0.y, u0) : make_float2(u0, v0.x);
-      const float2 w1 = xneg ? make_float2(v1.y, u1) : make_float2(u1, v1.x);
-      const float2 ax = f2s(au.x), ay = f2s(au.y);
-      carry[k] = f2lerp(ay, f2lerp(ax, w1, v1), f2lerp(ax, w0, v0));
+    for (int k = 0; k < DPT; ++k) {
+      carry[k] = make_float2(0.f, 0.f);
+      if (ok) {
+        const float4 au = t.au[i0 + k];
+        const bool xneg = __float_as_int(au.w) & 1;
+        carry[k] = bilinear(at(slot, 0, row_own, k), at(slot, 0, row_up, k), xneg ? 2 : -1, xneg,
+                            f2s(au.x), f2s(-au.x), f2s(au.y), f2s(-au.y));
+      }
     }
-    ++q;
   }
 
   double bud_a = 0.0, bud_b = 0.0;
   for (int b = 0; b < nbatch; ++b) {
+    const int q = b + 1;
     const int zb = zbeg + b * ZC;
     const int nb = min(ZC, zend - zb);
+    float2* part = part2 + (size_t)(b & 1) * G * ZC * 4 * 32;
+    // the lane's site coefficients, loaded now so that their latency
+    // overlaps the stream pass
+    float fka[ZC][2], fk0[ZC][2], flam[ZC][2], feta[ZC][2];
+#pragma unroll
+    for (int j = 0; j < ZC; ++j) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool okx = (xa + h < nx) && (j < nb);
+        const long long st = okx ? ((long long)(zb + j) * ny + y) * nx + xa + h : 0;
+        fka[j][h] = fld(cf.ka, cf.ka_s, st);
+        fk0[j][h] = fld(cf.k0, cf.k0_s, st);
+        flam[j][h] = fld(cf.lam, cf.lam_s, st);
+        feta[j][h] = fld(cf.eta, cf.eta_s, st);
+      }
+    }
+    issue(q + R - 1);
+    const bool ok = wait_item(q);
+    const float* slot = my_ring + (size_t)(q % R) * SLOT;
+    float2 Is[DPT][ZC];
     float2 aE[ZC], aX[ZC], aY[ZC], aZ[ZC];
 #pragma unroll
     for (int j = 0; j < ZC; ++j) aE[j] = aX[j] = aY[j] = aZ[j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < DPT; ++k) {
-      issue(q + R - 1);
-      const int i = g * DPT + k;
-      if (wait_item(q) && i < L.N) {
-        const float4 au = t.au[i];
-        const float4 nw = t.nw[i];
+#pragma unroll
+      for (int j = 0; j < ZC; ++j) Is[k][j] = make_float2(0.f, 0.f);
+      if (ok) {
+        const float4 au = t.au[i0 + k];
+        const float4 nw = t.nw[i0 + k];
         const int oct = __float_as_int(au.w);
         const bool xneg = oct & 1;
-        const int uc = xneg ? wc + 2 : wc - 1;
-        const float2 ax = f2s(au.x), ay = f2s(au.y);
-        const float2 az = f2s((oct & 4) ? 1.f - au.z : au.z);
+        const float2 ax = f2s(au.x), ay = f2s(au.y), nax = f2s(-au.x), nay = f2s(-au.y);
+        const float azw = zs ? 1.f - au.z : au.z;
+        const float2 az = f2s(azw), naz = f2s(-azw);
         const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z);
-        const float* slot = my_ring + (size_t)(q % R) * SLOT;
-        const int o0 = (oct & 2) ? 0 : BOXX, o1 = (oct & 2) ? BOXX : 0;
 #pragma unroll
         for (int j = 0; j < ZC; ++j) {
-          const float* r0 = slot + j * 2 * BOXX + o0;
-          const float* r1 = slot + j * 2 * BOXX + o1;
-          const float2 v0 = *reinterpret_cast<const float2*>(r0 + wc);
-          const float2 v1 = *reinterpret_cast<const float2*>(r1 + wc);
-          const float u0 = r0[uc], u1 = r1[uc];
-          const float2 w0 = xneg ? make_float2(v0.y, u0) : make_float2(u0, v0.x);
-          const float2 w1 = xneg ? make_float2(v1.y, u1) : make_float2(u1, v1.x);
-          const float2 Bn = f2lerp(ay, f2lerp(ax, w1, v1), f2lerp(ax, w0, v0));
-          // I* = (1 - a_z) B(z) + a_z B(z - sgn n^z); the carried plane is B(z - 1)
-          // for sgn = +1 and B(z) for sgn = -1
-          const float2 r = f2lerp(az, carry[k], Bn);
+          const float2 Bn = bilinear(at(slot, j, row_own, k), at(slot, j, row_up, k),
+                                     xneg ? 2 : -1, xneg, ax, nax, ay, nay);
+          // I* = (1 - a_z) B(z) + a_z B(z - sgn n^z): the carried plane is
+          // B(z - 1) for sgn = +1 and B(z) for sgn = -1
+          const float2 r = f2lerp(az, naz, carry[k], Bn);
           carry[k] = Bn;
-          Ist[((size_t)i * ZC + j) * 32 + lane] = r;
+          Is[k][j] = r;
           aE[j] = f2add(aE[j], r);
           aX[j] = f2fma(nx2, r, aX[j]);
           aY[j] = f2fma(ny2, r, aY[j]);
           aZ[j] = f2fma(nz2, r, aZ[j]);
         }
       }
-      ++q;
     }
 #pragma unroll
     for (int j = 0; j < ZC; ++j) {
@@ -348,76 +337,85 @@ k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const
       p[96] = aZ[j];
     }
     __syncthreads();
-    for (int item = g * 32 + lane; item < nb * 32; item += G * 32) {
-      const int j = item >> 5, l = item & 31;
+    // every warp sums the G partials of its own lanes' sites and forms the
+    // collision scalars itself (no second barrier; the partials are double
+    // buffered across batches)
+    float2 al[ZC], c0[ZC], c1x[ZC], c1y[ZC], c1z[ZC];
+    float ea = 0.f, eb = 0.f;  // this batch's budget terms, folded into FP64 below
+#pragma unroll
+    for (int j = 0; j < ZC; ++j) {
       float2 E = make_float2(0.f, 0.f), Fx = E, Fy = E, Fz = E;
       for (int qq = 0; qq < G; ++qq) {
-        const float2* p = part + (((size_t)qq * ZC + j) * 4) * 32 + l;
+        const float2* p = part + (((size_t)qq * ZC + j) * 4) * 32 + lane;
         E = f2add(E, p[0]);
         Fx = f2add(Fx, p[32]);
         Fy = f2add(Fy, p[64]);
         Fz = f2add(Fz, p[96]);
       }
-      const int xs = x0 + 2 * l;
-      const long long site = ((long long)(zb + j) * gr.ny + y) * nx + xs;
-      float2 o[5];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const bool ok = xs + h < nx;
-        const long long st = ok ? site + h : 0;
-        const float ka = fld(cf.ka, cf.ka_s, st), k0 = fld(cf.k0, cf.k0_s, st);
-        const float lam = fld(cf.lam, cf.lam_s, st), eta = fld(cf.eta, cf.eta_s, st);
         const float Es = h ? E.y : E.x;
-        const Coef c = collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, ka, k0, lam,
-                                       eta, Es, h ? Fx.y : Fx.x, h ? Fy.y : Fy.x, h ? Fz.y : Fz.x);
-        const float v[5] = {c.alpha, c.c0, c.c1x, c.c1y, c.c1z};
-#pragma unroll
-        for (int u = 0; u < 5; ++u) (h ? o[u].y : o[u].x) = v[u];
-        if (ok) {
-          bud_a += (double)Es;
-          bud_b += (double)c.Enew;
+        const Coef cc = collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, fka[j][h],
+                                        fk0[j][h], flam[j][h], feta[j][h], Es,
+                                        h ? Fx.y : Fx.x, h ? Fy.y : Fy.x, h ? Fz.y : Fz.x);
+        (h ? al[j].y : al[j].x) = cc.alpha;
+        (h ? c0[j].y : c0[j].x) = cc.c0;
+        (h ? c1x[j].y : c1x[j].x) = cc.c1x;
+        (h ? c1y[j].y : c1y[j].x) = cc.c1y;
+        (h ? c1z[j].y : c1z[j].x) = cc.c1z;
+        if (j < nb && xa + h < nx) {
+          ea += Es;
+          eb += cc.Enew;
         }
       }
-      float2* cp = coef + ((size_t)j * 5) * 32 + l;
-#pragma unroll
-      for (int u = 0; u < 5; ++u) cp[u * 32] = o[u];
     }
-    __syncthreads();
-    float2 al[ZC], c0[ZC], c1x[ZC], c1y[ZC], c1z[ZC];
-#pragma unroll
-    for (int j = 0; j < ZC; ++j) {
-      const float2* cp = coef + ((size_t)j * 5) * 32 + lane;
-      al[j] = cp[0];
-      c0[j] = cp[32];
-      c1x[j] = cp[64];
-      c1y[j] = cp[96];
-      c1z[j] = cp[128];
+    if (L.budget_partials && g == 0) {
+      bud_a += (double)ea;
+      bud_b += (double)eb;
     }
-    if (alive) {
-      // interior sites with no ghost mirror take the float2 fast path
-      const bool yz_edge = (gr.periodic[1] && (y == 0 || y == gr.ny - 1)) || gr.periodic[2];
-      const bool x_edge = gr.periodic[0] && (xa == 0 || xa + 1 >= nx - 1);
+    if (alive && in0) {
+      // x ghost columns this lane mirrors into (periodic x): column GL - 1
+      // holds x = nx - 1, column nx + GL holds x = 0
+      const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
+      const bool gx_hi = gr.periodic[0] && xa == 0;
+      const bool lo_from_y = xa + 1 == nx - 1;
+      const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
 #pragma unroll
       for (int k = 0; k < DPT; ++k) {
-        const int i = g * DPT + k;
-        if (i < L.N) {
-          const float4 nw = t.nw[i];
-          const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z), w2 = f2s(nw.w);
+        const float4 nw = t.nw[i0 + k];
+        if (__float_as_int(t.au[i0 + k].w) & 8) continue;  // inert padding direction
+        const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z), w2 = f2s(nw.w);
 #pragma unroll
-          for (int j = 0; j < ZC; ++j) {
-            if (j < nb && in0) {
-              const int z = zb + j;
-              const float2 r = Ist[((size_t)i * ZC + j) * 32 + lane];
-              const float2 eq =
-                  f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j])));
-              const float2 o = f2fma(al[j], r, f2mul(w2, eq));
-              const bool mirror = x_edge || (yz_edge && (y == 0 || y == gr.ny - 1 ||
-                                                         z == 0 || z == nz - 1));
-              if (in1 && !mirror) {
-                *reinterpret_cast<float2*>(out + pidx(gr, i, z, y, xa)) = o;
-              } else {
-                store_pop(out, gr, i, z, y, xa, o.x);
-                if (in1) store_pop(out, gr, i, z, y, xa + 1, o.y);
+        for (int j = 0; j < ZC; ++j) {
+          if (j < nb) {
+            const int z = zb + j;
+            const float2 eq = f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j])));
+            const float2 o = f2fma(al[j], Is[k][j], f2mul(w2, eq));
+            const float vlo = lo_from_y ? o.y : o.x;
+            const bool z_face = gr.periodic[2] && (z == 0 || z == nz - 1);
+            if (!(y_face || z_face)) {
+              float* base = out + (long long)(i0 + k) * gr.si + (long long)(z + 1) * gr.sz +
+                            (long long)(y + 1) * gr.sy;
+              if (in1) *reinterpret_cast<float2*>(base + xa + GL) = o;
+              else base[xa + GL] = o.x;
+              if (gx_lo) base[GL - 1] = vlo;
+              if (gx_hi) base[nx + GL] = o.x;
+            } else {
+              // a row or plane on a periodic face: every (row, plane) image
+              const int rows[3] = {y + 1, (gr.periodic[1] && y == ny - 1) ? 0 : -1,
+                                   (gr.periodic[1] && y == 0) ? ny + 1 : -1};
+              const int planes[3] = {z + 1, (gr.periodic[2] && z == nz - 1) ? 0 : -1,
+                                     (gr.periodic[2] && z == 0) ? nz + 1 : -1};
+#pragma unroll 1
+              for (int cmb = 0; cmb < 9; ++cmb) {
+                const int rr = rows[cmb % 3], pp = planes[cmb / 3];
+                if (rr < 0 || pp < 0) continue;
+                float* base = out + (long long)(i0 + k) * gr.si + (long long)pp * gr.sz +
+                              (long long)rr * gr.sy;
+                base[xa + GL] = o.x;
+                if (in1) base[xa + GL + 1] = o.y;
+                if (gx_lo) base[GL - 1] = vlo;
+                if (gx_hi) base[nx + GL] = o.x;
               }
             }
           }
@@ -426,8 +424,12 @@ k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const
     }
   }
   // every issued copy must land before the CTA's shared memory is released
-  for (int qq = q; qq < issued; ++qq)
+  for (int qq = nbatch + 1; qq < issued; ++qq)
     mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), L.err);
+  if (!alive) {
+    for (int qq = 0; qq < issued; ++qq)
+      mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), L.err);
+  }
   if (L.budget_partials) {
     for (int s = 16; s > 0; s >>= 1) {
       bud_a += __shfl_xor_sync(0xffffffffu, bud_a, s);
@@ -443,52 +445,68 @@ k_tma_static(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const
 }
 
 template <int DPT, int ZC, int R>
-size_t tma_smem(int G) {
-  return sizeof(float) * (size_t)G * R * slot_floats<ZC>() +
-         sizeof(float2) * 32 * ((size_t)G * DPT * ZC + (size_t)G * ZC * 4 + ZC * 5) + 8 * G * R +
-         16;
+size_t step_smem(int G) {
+  return sizeof(float) * (size_t)G * R * slot_floats<DPT, ZC>() +
+         sizeof(float2) * 32 * ((size_t)2 * G * ZC * 4) + 8 * (size_t)G * R + 16;
 }
 
-template <int DPT, int ZC, int R>
-cudaError_t launch_tma(const StepLaunch& L, const StaticCoef& c, const DirTable& t, int G,
-                       int zchunk, cudaStream_t s, int* nblocks) {
+template <int DPT, int ZC, int R, int MAXT>
+cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable& t, int zchunk,
+                       cudaStream_t s, int* nblocks) {
+  const int G = L.N / DPT;  // internal (padded) direction count / directions per warp
+  if (!L.tmap_in || G < 1 || G * DPT != L.N || 32 * G > MAXT) return cudaErrorInvalidValue;
   dim3 block(32, G);
   dim3 grid((L.g.nx + 63) / 64, L.g.ny, (L.g.nz + zchunk - 1) / zchunk);
   const long long nb_ = (long long)grid.x * grid.y * grid.z;
   if (L.budget_partials && nb_ > L.partials_cap) return cudaErrorInvalidValue;
   if (nblocks) *nblocks = (int)nb_;
-  const size_t smem = tma_smem<DPT, ZC, R>(G);
-  if (smem > 227 * 1024 || !L.tmap_in) return cudaErrorInvalidValue;
+  const size_t smem = step_smem<DPT, ZC, R>(G);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !(attr_set >> dev & 1ull)) {
     const cudaError_t e = cudaFuncSetAttribute(
-        k_tma_static<DPT, ZC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        k_step_f32<DPT, ZC, R, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set |= 1ull << dev;
   }
-  k_tma_static<DPT, ZC, R><<<grid, block, smem, s>>>(*L.tmap_in, L, c, t, zchunk);
+  k_step_f32<DPT, ZC, R, MAXT><<<grid, block, smem, s>>>(*L.tmap_in, L, c, t, zchunk);
   return cudaGetLastError();
 }
 
+constexpr int kRing = 2;
+
 }  // namespace
 
-int tma_planes_per_batch(int N) { return N <= 48 ? 2 : 1; }
+// Compiled tile plans (directions per warp, planes per batch, thread cap of
+// the launch bounds), in order of preference for the host's planner, which
+// also checks the shared-memory need with step_tile_smem().
+const int kTilePlans[][3] = {{5, 2, 512}, {10, 1, 640}, {8, 2, 512}, {4, 2, 512}, {4, 1, 768}};
+const int kNumTilePlans = 5;
 
-// Direction groups of 8 (N <= 48, 2 planes per batch) or 21 (larger sets,
-// 1 plane per batch: shared memory holds I* of every direction of a batch);
-// z chunks of 32 planes.
-cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
-                              cudaStream_t s, int* nblocks) {
-  const int N = L.N;
-  const int zchunk = 32;
-  if (N <= 48) return launch_tma<8, 2, 4>(L, c, t, (N + 7) / 8, zchunk, s, nblocks);
-  return launch_tma<21, 1, 4>(L, c, t, (N + 20) / 21, zchunk, s, nblocks);
+size_t step_tile_smem(int dpt, int zc, int warps) {
+  if (dpt == 5 && zc == 2) return step_smem<5, 2, kRing>(warps);
+  if (dpt == 10 && zc == 1) return step_smem<10, 1, kRing>(warps);
+  if (dpt == 8 && zc == 2) return step_smem<8, 2, kRing>(warps);
+  if (dpt == 4 && zc == 2) return step_smem<4, 2, kRing>(warps);
+  if (dpt == 4 && zc == 1) return step_smem<4, 1, kRing>(warps);
+  return (size_t)-1;
 }
 
-bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int N, void* base, int zc,
+cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
+                              int dpt, int zc, cudaStream_t s, int* nblocks) {
+  const int zchunk = 32;
+  if (dpt == 5 && zc == 2) return launch_f32<5, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
+  if (dpt == 10 && zc == 1) return launch_f32<10, 1, kRing, 640>(L, c, t, zchunk, s, nblocks);
+  if (dpt == 8 && zc == 2) return launch_f32<8, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
+  if (dpt == 4 && zc == 2) return launch_f32<4, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
+  if (dpt == 4 && zc == 1) return launch_f32<4, 1, kRing, 768>(L, c, t, zchunk, s, nblocks);
+  return cudaErrorInvalidValue;
+}
+
+bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int dpt, int zc,
                          std::string& err) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -502,11 +520,13 @@ bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int N, void* base, int
     }
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)g.PX, (cuuint64_t)g.PY, (cuuint64_t)g.PZ * N};
-  const cuuint64_t strides[2] = {(cuuint64_t)g.PX * 4, (cuuint64_t)g.plane * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)BOXX, 2, (cuuint32_t)zc};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box,
+  const cuuint64_t dims[4] = {(cuuint64_t)g.PX, (cuuint64_t)Ni, (cuuint64_t)g.PY,
+                              (cuuint64_t)g.PZ};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.si * 4, (cuuint64_t)g.sy * 4,
+                                 (cuuint64_t)g.sz * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)BOXX, (cuuint32_t)dpt, 2, (cuuint32_t)zc};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

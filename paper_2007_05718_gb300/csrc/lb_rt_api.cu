@@ -14,7 +14,12 @@ using namespace lbrt;
 struct lb_rt {
   lb_rt_config cfg{};
   Grid grid{};
-  int N = 0;
+  int N = 0;                    // directions, external (user) order
+  int Ni = 0;                   // internal directions including inert padding
+  int dpt = 0, zc = 0;          // tile plan of the static kernel
+  std::vector<int> ext_of_int;  // internal -> external index (-1: padding)
+  std::vector<int> int_of_ext;  // external -> internal index
+  int* d_int_of_ext = nullptr;  // device copy
   double dt = 0.0;
   std::vector<double> n, w;
   DirTable table{};
@@ -117,12 +122,82 @@ std::vector<float> balanced_weights(const std::vector<double>& w) {
   return f;
 }
 
+// Internal direction order.  Directions are grouped by their upwind (row,
+// plane) class (sgn n^y, sgn n^z); inside a class by sgn n^x, then by the
+// external index.  For the static TMA kernel every class is padded to a
+// multiple of the plan's directions per warp with inert entries, so that a
+// warp's directions share one upwind row and one plane shift and load as a
+// single box.  The plan (directions per warp, planes per batch) is the one
+// with the least padding among the compiled tile plans that fit in shared
+// memory.  Moving-fluid handles keep the external order.
+void plan_directions(lb_rt* h) {
+  const int N = h->N;
+  h->ext_of_int.clear();
+  h->int_of_ext.assign(N, -1);
+  if (h->cfg.moving) {
+    for (int e = 0; e < N; ++e) h->ext_of_int.push_back(e);
+    h->dpt = h->zc = 0;
+  } else {
+    std::vector<std::vector<int>> cls(4);
+    for (int e = 0; e < N; ++e) {
+      const int c = (h->n[3 * e + 1] < 0 ? 1 : 0) | (h->n[3 * e + 2] < 0 ? 2 : 0);
+      cls[c].push_back(e);
+    }
+    for (auto& c : cls)
+      std::stable_sort(c.begin(), c.end(), [&](int a, int b) {
+        return (h->n[3 * a] < 0) < (h->n[3 * b] < 0);
+      });
+    int best = -1, best_ni = 1 << 30;
+    for (int p = 0; p < kNumTilePlans; ++p) {
+      const int dpt = kTilePlans[p][0], zc = kTilePlans[p][1];
+      if (zc > 1 && zc > h->grid.nz) continue;
+      int ni = 0;
+      for (auto& c : cls) ni += (int)(c.size() + dpt - 1) / dpt * dpt;
+      const int warps = ni / dpt;
+      if (ni > kMaxInternalDirs || 32 * warps > kTilePlans[p][2]) continue;
+      if (step_tile_smem(dpt, zc, warps) > 227 * 1024) continue;
+      if (ni < best_ni) {
+        best = p;
+        best_ni = ni;
+      }
+    }
+    h->dpt = best >= 0 ? kTilePlans[best][0] : 0;
+    h->zc = best >= 0 ? kTilePlans[best][1] : 0;
+    for (auto& c : cls) {
+      for (int e : c) h->ext_of_int.push_back(e);
+      if (h->dpt)
+        for (size_t k = c.size(); k % h->dpt; ++k) h->ext_of_int.push_back(-1);
+    }
+  }
+  h->Ni = (int)h->ext_of_int.size();
+  for (int i = 0; i < h->Ni; ++i)
+    if (h->ext_of_int[i] >= 0) h->int_of_ext[h->ext_of_int[i]] = i;
+}
+
 void fill_table(lb_rt* h) {
   std::memset(&h->table, 0, sizeof(h->table));
   const std::vector<float> wf = balanced_weights(h->w);
-  for (int i = 0; i < h->N; ++i) {
-    const double* q = &h->n[3 * i];
-    h->table.nw[i] = make_float4((float)q[0], (float)q[1], (float)q[2], wf[i]);
+  for (int i = 0; i < h->Ni; ++i) {
+    const int e = h->ext_of_int[i];
+    if (e < 0) {
+      // inert padding entry: no weight, no direction, the class of its
+      // predecessor (its slot is part of that class's group), bit 3 set
+      int oct = 8;
+      if (i > 0) {
+        float prev;
+        std::memcpy(&prev, &h->table.au[i - 1].w, sizeof(float));
+        int po;
+        std::memcpy(&po, &prev, sizeof(int));
+        oct |= po & 6;
+      }
+      float octf;
+      std::memcpy(&octf, &oct, sizeof(float));
+      h->table.nw[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      h->table.au[i] = make_float4(0.f, 0.f, 0.f, octf);
+      continue;
+    }
+    const double* q = &h->n[3 * e];
+    h->table.nw[i] = make_float4((float)q[0], (float)q[1], (float)q[2], wf[e]);
     int oct = (q[0] < 0 ? 1 : 0) | (q[1] < 0 ? 2 : 0) | (q[2] < 0 ? 4 : 0);
     float octf;
     std::memcpy(&octf, &oct, sizeof(float));
@@ -143,7 +218,7 @@ lb_rt_status copy_in(lb_rt* h, void* dst, const void* src, size_t bytes, int ptr
 
 lb_rt_status reset_budget(lb_rt* h) {
   CK(h, cudaMemsetAsync(h->acc, 0, 8 * sizeof(double), h->stream));
-  cudaError_t e = launch_total_energy(h->grid, h->N, h->pop[h->cur], h->cfg.storage,
+  cudaError_t e = launch_total_energy(h->grid, h->Ni, h->pop[h->cur], h->cfg.storage,
                                       h->partials, h->partials_cap, h->acc, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "total energy");
   CK(h, cudaMemcpyAsync(h->acc + 1, h->acc, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -211,8 +286,12 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   h->grid.PX = ((cfg->nx + GL + 1) + 7) / 8 * 8;
   h->grid.PY = cfg->ny + 2;
   h->grid.PZ = cfg->nz + 2;
-  h->grid.plane = (long long)h->grid.PX * h->grid.PY;
-  h->grid.dstride = h->grid.plane * h->grid.PZ;
+  plan_directions(h);
+  if (!h->cfg.moving && !h->dpt) return bad("no tile plan fits this direction set");
+  h->grid.si = h->grid.PX;
+  h->grid.sy = (long long)h->Ni * h->grid.PX;
+  h->grid.sz = h->grid.sy * h->grid.PY;
+  h->grid.total = h->grid.sz * h->grid.PZ;
   h->dt = cfg->cfl * cfg->dx;
   fill_table(h);
 
@@ -228,7 +307,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     h->own_stream = (e == cudaSuccess);
   }
-  h->pop_bytes = (size_t)h->grid.dstride * h->N * elem_bytes(cfg->storage);
+  h->pop_bytes = (size_t)h->grid.total * elem_bytes(cfg->storage);
   const int max_blocks = 4096;
   auto alloc = [&](void** p, size_t b) {
     if (e != cudaSuccess) return;
@@ -246,6 +325,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   h->partials_cap = (int)std::max<long long>(max_blocks, step_blocks);
   alloc((void**)&h->partials, sizeof(double) * 2 * h->partials_cap);
   alloc((void**)&h->acc, sizeof(double) * 8);
+  alloc((void**)&h->d_int_of_ext, sizeof(int) * h->N);
   alloc((void**)&h->err, sizeof(unsigned));
   if (e != cudaSuccess) {
     g_create_msg = std::string("allocation: ") + cudaGetErrorString(e);
@@ -259,6 +339,9 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, h->pop_bytes, h->stream);
   if (e == cudaSuccess && h->ef[0]) e = cudaMemsetAsync(h->ef[0], 0, sizeof(float4) * sites, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_int_of_ext, h->int_of_ext.data(), sizeof(int) * h->N,
+                        cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -268,9 +351,8 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   }
   if (cfg->storage == LB_RT_F32 && !cfg->moving) {
     std::string terr;
-    const int zc = tma_planes_per_batch(h->N);
     for (int b = 0; b < 2; ++b) {
-      if (!make_pop_tensor_map(&h->tmap[b], h->grid, h->N, h->pop[b], zc, terr)) {
+      if (!make_pop_tensor_map(&h->tmap[b], h->grid, h->Ni, h->pop[b], h->dpt, h->zc, terr)) {
         g_create_msg = terr;
         lb_rt_destroy(h);
         return LB_RT_ECUDA;
@@ -292,6 +374,7 @@ void lb_rt_destroy(lb_rt* h) {
   cudaFree(h->frozen_vals);
   cudaFree(h->partials);
   cudaFree(h->acc);
+  cudaFree(h->d_int_of_ext);
   cudaFree(h->err);
   cudaFree(h->scratch);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -367,8 +450,8 @@ lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind
     return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   }
   h->cur = 0;
-  cudaError_t e = launch_init_state(h->grid, h->N, src, kind, h->pop[0], h->cfg.storage,
-                                    h->table, h->stream);
+  cudaError_t e = launch_init_state(h->grid, h->Ni, h->N, h->d_int_of_ext, src, kind, h->pop[0],
+                                    h->cfg.storage, h->table, h->stream);
   if (tmp) {
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
@@ -410,7 +493,9 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     StepLaunch L{};
     L.g = h->grid;
-    L.N = h->N;
+    L.N = h->Ni;
+    L.dpt = h->dpt;
+    L.zc = h->zc;
     L.dt = (float)h->dt;
     L.collision = h->cfg.collision;
     L.lambda_iters = h->cfg.lambda_iters;
@@ -431,8 +516,8 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     ++launches;
     if (h->nfrozen) {
-      e = launch_frozen(h->grid, h->N, h->nfrozen, h->frozen_cells, h->frozen_vals,
-                        h->pop[h->cur ^ 1], h->cfg.storage,
+      e = launch_frozen(h->grid, h->N, h->d_int_of_ext, h->nfrozen, h->frozen_cells,
+                        h->frozen_vals, h->pop[h->cur ^ 1], h->cfg.storage,
                         h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
     }
@@ -475,7 +560,7 @@ lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P, lb_rt_budget*
       dF = F ? h->scratch + S : nullptr;
       dP = P ? h->scratch + 4 * S : nullptr;
     }
-    cudaError_t e = launch_moments(h->grid, h->N, h->pop[h->cur], h->cfg.storage,
+    cudaError_t e = launch_moments(h->grid, h->Ni, h->pop[h->cur], h->cfg.storage,
                                    h->table, dE, dF, dP, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     if (ptr_kind == LB_RT_HOST) {
@@ -510,7 +595,8 @@ lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
   } else if (ptr_kind != LB_RT_DEVICE) {
     return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   }
-  cudaError_t e = launch_decode(h->grid, h->N, h->pop[h->cur], h->cfg.storage, dst, h->stream);
+  cudaError_t e =
+      launch_decode(h->grid, h->N, h->d_int_of_ext, h->pop[h->cur], h->cfg.storage, dst, h->stream);
   if (e == cudaSuccess && tmp)
     e = cudaMemcpyAsync(out, tmp, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(h->stream);

@@ -21,21 +21,29 @@ namespace lbrt {
 // a = cfl |n| the weight of the upwind corner along each axis in Eq. (interp);
 // octant bit k set means sgn(n_k) = -1, i.e. the pull reads the +1 neighbour
 // along axis k.
+// The table is in the library's internal direction order (see the planner in
+// lb_rt_api.cu): directions grouped by (sgn n^y, sgn n^z), each group padded
+// with inert entries (w = 0, n = 0, octant bit 3 set) whose populations stay 0.
+constexpr int kMaxInternalDirs = 256;
 struct DirTable {
-  float4 nw[LB_RT_MAX_DIRS];
-  float4 au[LB_RT_MAX_DIRS];
+  float4 nw[kMaxInternalDirs];
+  float4 au[kMaxInternalDirs];
 };
 
-// Device layout of a population buffer.  Every direction holds a padded
-// block [PZ][PY][PX] with one ghost layer around the nz x ny x nx interior:
-// site (x, y, z) lives at column x + GL, row y + 1, plane z + 1.  GL = 2
-// keeps even x at even columns (8-byte pairs); PX is rounded up so that rows
-// start on 16-byte boundaries (TMA strides) in every storage type.  Ghost
-// cells of a periodic axis mirror the opposite interior edge (column 1 <-
-// x = nx - 1, column nx + GL <- x = 0, row 0 <- y = ny - 1, row ny + 1 <- y = 0,
-// plane 0 <- z = nz - 1, plane nz + 1 <- z = 0); on a vacuum axis they stay 0.
-// Every kernel that writes populations also writes the mirrors, so a pull
-// from x - 1, y - 1 or z - 1 (or + 1) never needs boundary logic.
+// Device layout of a population buffer: [PZ][PY][N][PX], x fastest.  The
+// interior nz x ny x nx grid sits inside one ghost layer: site (x, y, z) of
+// direction i is element i * si + (z + 1) * sz + (y + 1) * sy + x + GL with
+// si = PX, sy = N * PX, sz = N * PX * PY.  Keeping the N rows of one (y, z)
+// next to each other keeps every CTA's working set (all directions of a few
+// rows) within a few contiguous megabytes instead of N blocks that are
+// gigabytes apart.  GL = 2 keeps even x at even columns (8-byte pairs); PX is
+// a multiple of 8 so that rows start on 16-byte boundaries (TMA strides) in
+// every storage type.  Ghost cells of a periodic axis mirror the opposite
+// interior edge (column 1 <- x = nx - 1, column nx + GL <- x = 0, row 0 <-
+// y = ny - 1, row ny + 1 <- y = 0, plane 0 <- z = nz - 1, plane nz + 1 <- z = 0);
+// on a vacuum axis they stay 0.  Every kernel that writes populations also
+// writes the mirrors, so a pull from x - 1, y - 1 or z - 1 (or + 1) never
+// needs boundary logic.
 constexpr int GL = 2;
 
 struct Grid {
@@ -44,13 +52,12 @@ struct Grid {
   long long sites;   // nx * ny * nz
   int periodic[3];   // per axis x, y, z
   int PX, PY, PZ;    // padded extents
-  long long plane;   // PX * PY
-  long long dstride; // PX * PY * PZ: elements per direction
+  long long si, sy, sz;  // element strides of direction, row and plane
+  long long total;   // elements of one buffer: sz * PZ
 };
 
 __host__ __device__ inline long long pidx(const Grid& g, int i, int z, int y, int x) {
-  return (long long)i * g.dstride + (long long)(z + 1) * g.plane + (long long)(y + 1) * g.PX +
-         (x + GL);
+  return (long long)i * g.si + (long long)(z + 1) * g.sz + (long long)(y + 1) * g.sy + (x + GL);
 }
 
 // Site coefficient fields (dense [nz][ny][nx]): nullptr means "use the scalar".
@@ -69,7 +76,8 @@ enum StorageKind { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
 struct StepLaunch {
   Grid g;
-  int N;
+  int N;               // internal direction count (padding included)
+  int dpt, zc;         // tile plan of the static kernel: directions per warp, planes per batch
   float dt;
   int collision;       // LB_RT_IMPLICIT_EXACT / LB_RT_EXPLICIT / LB_RT_LAMBDA_K
   int lambda_iters;
@@ -87,24 +95,31 @@ cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const D
                                int storage, cudaStream_t s, int* nblocks);
 cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks);
-cudaError_t launch_moments(const Grid& g, int N, const void* pop, int storage,
+// Ni = internal direction count; Next = external (user) count; int_of_ext =
+// device array mapping an external direction index to its internal one.
+cudaError_t launch_moments(const Grid& g, int Ni, const void* pop, int storage,
                            const DirTable& t, float* E, float* F, float* P, cudaStream_t s);
-cudaError_t launch_init_state(const Grid& g, int N, const float* data, int kind, void* pop,
-                              int storage, const DirTable& t, cudaStream_t s);
-cudaError_t launch_decode(const Grid& g, int N, const void* pop, int storage, float* out,
-                          cudaStream_t s);
-cudaError_t launch_frozen(const Grid& g, int N, int ncells, const int64_t* cells, const float* vals,
-                          void* pop, int storage, double* injection_acc, cudaStream_t s);
+cudaError_t launch_init_state(const Grid& g, int Ni, int Next, const int* int_of_ext,
+                              const float* data, int kind, void* pop, int storage,
+                              const DirTable& t, cudaStream_t s);
+cudaError_t launch_decode(const Grid& g, int Next, const int* int_of_ext, const void* pop,
+                          int storage, float* out, cudaStream_t s);
+cudaError_t launch_frozen(const Grid& g, int Next, const int* int_of_ext, int ncells,
+                          const int64_t* cells, const float* vals, void* pop, int storage,
+                          double* injection_acc, cudaStream_t s);
 cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* acc,
                                    cudaStream_t s);
 cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, int storage,
                                 double* partials, int max_blocks, double* out, cudaStream_t s);
 
-// TMA descriptor of a padded float32 population buffer viewed as the 3D
-// tensor [N * PZ][PY][PX] with box (68, 2, zc) (kernels_tma.cu).
-bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int N, void* base, int zc,
+// TMA descriptor of a padded float32 population buffer viewed as the 4D
+// tensor [PZ][PY][Ni][PX] with box (68, dpt, 2, zc) (kernels_tma.cu), and the
+// tile plans the static kernel is compiled for.
+bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int dpt, int zc,
                          std::string& err);
-int tma_planes_per_batch(int N);
+extern const int kTilePlans[][3];
+extern const int kNumTilePlans;
+size_t step_tile_smem(int dpt, int zc, int warps);
 
 // Direction sets built on the host (directions.cpp).
 bool build_directions(const lb_rt_config& cfg, std::vector<double>& n, std::vector<double>& w,
@@ -133,11 +148,11 @@ __device__ __forceinline__ void store_pop(T* pop, const Grid& g, int i, int z, i
   const int nxs = mirrors(x, g.nx, g.periodic[0], GL, xs);
   const int nys = mirrors(y, g.ny, g.periodic[1], 1, ys);
   const int nzs = mirrors(z, g.nz, g.periodic[2], 1, zs);
-  const long long base = (long long)i * g.dstride;
+  const long long base = (long long)i * g.si;
   for (int a = 0; a < nzs; ++a)
     for (int b = 0; b < nys; ++b)
       for (int c = 0; c < nxs; ++c)
-        pop[base + (long long)zs[a] * g.plane + (long long)ys[b] * g.PX + xs[c]] = v;
+        pop[base + (long long)zs[a] * g.sz + (long long)ys[b] * g.sy + xs[c]] = v;
 }
 
 // True when site (x, y, z) has at least one ghost mirror.
