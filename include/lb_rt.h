@@ -189,8 +189,28 @@ lb_rt_status lb_rt_directions(const lb_rt* h, int* ndir, double* dirs, double* w
 lb_rt_status lb_rt_enable_timing(lb_rt* h, int on);
 lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch);
 
+/* FP64 total energy sum_sites sum_i I_i of a dense float32 population array
+ * pop [ndir][sites] in device memory (for example the output of
+ * lb_rt_get_populations with a device pointer), computed without allocating
+ * anything.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc where they need the number -- code running while
+ * another framework owns the device memory pool, a real-time loop that may not
+ * pay allocation latency, or a process whose device memory budget is fixed in
+ * advance.  The per-block partial sums live in a fixed 32 KB array that every
+ * GPU loading the library holds until exit, which limits sites to
+ * 16,777,216 (larger inputs return LB_RT_EINVAL).  out is a device pointer
+ * (ptr_kind = LB_RT_DEVICE: the result is written stream-ordered on `stream`)
+ * or a host pointer (LB_RT_HOST: the call synchronises `stream`).  The first
+ * call on a device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (for example on two streams) race.  Errors: EINVAL (bad
+ * argument or too many sites), ECUDA; lb_rt_last_error(NULL) says which. */
+lb_rt_status lb_rt_total_energy_noalloc(const float* pop, int ndir, long long sites, double* out,
+                                        int ptr_kind, void* stream);
+
 /* Message of the last error on h; with h == NULL, why the calling thread's
- * last lb_rt_create() failed. */
+ * last failed call without a handle (lb_rt_create(),
+ * lb_rt_total_energy_noalloc()) failed. */
 const char* lb_rt_last_error(const lb_rt* h);
 const char* lb_rt_version(void);
 

@@ -227,6 +227,9 @@ lb_rt_status reset_budget(lb_rt* h) {
 
 }  // namespace
 
+// Message for lb_rt_last_error(NULL) from a failed call that has no handle.
+void lbrt::set_unbound_error(const std::string& m) { g_create_msg = m; }
+
 extern "C" {
 
 const char* lb_rt_version(void) { return "lbrt 0.1 (sm_103a)"; }

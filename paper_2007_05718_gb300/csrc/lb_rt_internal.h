@@ -121,6 +121,9 @@ extern const int kTilePlans[][3];
 extern const int kNumTilePlans;
 size_t step_tile_smem(int dpt, int zc, int warps);
 
+// Message returned by lb_rt_last_error(NULL) on this thread (calls without a handle).
+void set_unbound_error(const std::string& m);
+
 // Direction sets built on the host (directions.cpp).
 bool build_directions(const lb_rt_config& cfg, std::vector<double>& n, std::vector<double>& w,
                       std::string& err);

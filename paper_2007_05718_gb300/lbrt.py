@@ -28,6 +28,7 @@ EXPORTED = [
     "lb_rt_moments", "lb_rt_get_populations", "lb_rt_state_bytes", "lb_rt_save_state",
     "lb_rt_restore_state", "lb_rt_sync", "lb_rt_directions", "lb_rt_enable_timing",
     "lb_rt_last_step_ms", "lb_rt_last_error", "lb_rt_version", "lb_rt_destroy",
+    "lb_rt_total_energy_noalloc",
 ]
 
 
@@ -100,6 +101,8 @@ def load(path=LIB_PATH):
         "lb_rt_last_error": (C.c_char_p, [H]),
         "lb_rt_version": (C.c_char_p, []),
         "lb_rt_destroy": (None, [H]),
+        "lb_rt_total_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
+                                                 C.c_int, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -317,3 +320,24 @@ def lb_rt_last_error(h):
 
 def lb_rt_version():
     return load().lb_rt_version().decode()
+
+
+def lb_rt_total_energy_noalloc(pop, ndir, sites, out=None, stream=None):
+    """FP64 total energy of a dense device population array [ndir][sites]
+    without any allocation inside the library.  With out=None the result is
+    returned as a Python float (host output); otherwise `out` is a float64
+    CUDA tensor of one element that receives it on the device."""
+    p, pk = _ptr(pop)
+    if pk != LB_RT_DEVICE:
+        raise ValueError("populations must be a CUDA tensor")
+    lib = load()
+    if out is None:
+        res = C.c_double()
+        _check(None, lib.lb_rt_total_energy_noalloc(p, ndir, sites, C.byref(res), LB_RT_HOST,
+                                                    stream or None))
+        return res.value
+    op, ok = _ptr(out)
+    if ok != LB_RT_DEVICE:
+        raise ValueError("out must be a CUDA tensor")
+    _check(None, lib.lb_rt_total_energy_noalloc(p, ndir, sites, op, LB_RT_DEVICE, stream or None))
+    return out
