@@ -176,38 +176,67 @@ __device__ __forceinline__ float2 bilinear(const float* r0, const float* r1, int
   return f2lerp(ay, nay, f2lerp(ax, nax, w1, v1), f2lerp(ax, nax, w0, v0));
 }
 
-template <int DPT, int ZC, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1)
+// Tile schedule of the persistent grid: tile ti covers the 64 columns
+// x0 .. x0 + 63 of row y over the planes zbeg .. zbeg + zlen - 1; tiles are
+// numbered x-block fastest, then y, then z chunk, and CTA b takes tiles b,
+// b + gridDim.x, ...  so that the tiles in flight at one time are
+// neighbouring rows whose shared upwind rows meet in L2.  The nz planes are
+// split into nzc chunks of near-equal length.
+struct TileGeom {
+  int x0, y, zbeg, zlen;
+};
+__device__ __forceinline__ TileGeom tile_geom(int ti, int nxb, int ny, int nz, int nzc) {
+  TileGeom tg;
+  tg.x0 = (ti % nxb) * 64;
+  const int r = ti / nxb;
+  tg.y = r % ny;
+  const int c = r / ny;
+  const int base = nz / nzc, rem = nz % nzc;
+  tg.zbeg = c * base + min(c, rem);
+  tg.zlen = base + (c < rem ? 1 : 0);
+  return tg;
+}
+
+// Per tile the kernel walks the planes B(zbeg - 1) .. B(zbeg + zlen - 1) of
+// the in-plane (bilinear) values, ZC planes per item; item m, plane j yields
+// the output plane z = zbeg - 1 + m ZC + j (for both signs of n^z, with the
+// box shifted by one plane for sgn n^z = -1), which is stored when it lies in
+// the tile; the first plane of a tile only seeds the carried value.
+template <int ZC>
+__device__ __forceinline__ int tile_items(int zlen) {
+  return (zlen + 1 + ZC - 1) / ZC;
+}
+
+template <int DPT, int ZC, int R, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const StaticCoef cf,
-           const DirTable t, int zchunk) {
+           const DirTable t) {
   constexpr int SLOT = slot_floats<DPT, ZC>();
+  static_assert(SLOT >= ZC * 4 * 64, "the partial moments must fit in a consumed slot");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
   const Grid& gr = L.g;
   const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
-  // shared layout: ring [G][R][SLOT] | part [2][G][ZC][4][32] float2 | mbar [G][R] | abort flag
+  // shared layout: ring [G][R][SLOT] | coef [ZC][5][64] | mbar [G][R] |
+  // budget [2 ZC][2] double | abort flag
   float* ring = reinterpret_cast<float*>(smem_raw);
-  float2* part2 = reinterpret_cast<float2*>(ring + (size_t)G * R * SLOT);
-  unsigned long long* mbar =
-      reinterpret_cast<unsigned long long*>(part2 + (size_t)2 * G * ZC * 4 * 32);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(mbar + G * R);
+  float* coef = ring + (size_t)G * R * SLOT;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(coef + ZC * 5 * 64);
+  double* bsum = reinterpret_cast<double*>(mbar + G * R);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 4 * ZC);
 
-  const int x0 = blockIdx.x * 64;
-  const int xa = x0 + 2 * lane;  // the lane's pair (xa, xa + 1)
-  const bool in0 = xa < nx, in1 = xa + 1 < nx;
-  const int y = blockIdx.y;
-  const int zbeg = blockIdx.z * zchunk;
-  const int zend = min(zbeg + zchunk, nz);
+  const int nxb = (nx + 63) / 64;
+  const int ntiles = nxb * ny * L.nzc;
   const float inv_d = 1.f / (float)gr.dims;
   float* __restrict__ out = static_cast<float*>(L.out);
-  const int nbatch = (zend - zbeg + ZC - 1) / ZC;
   const int i0 = g * DPT;
   // the warp's row / plane class (uniform over its directions)
   const int oct0 = __float_as_int(t.au[i0].w);
   const bool yneg = oct0 & 2;
   const int zs = (oct0 & 4) ? 1 : 0;
   const int row_own = yneg ? 0 : 1, row_up = yneg ? 1 : 0;
+  const int nunits = 2 * ZC;  // coefficient units: (plane, half row) pairs of a batch
 
   if (lane == 0) {
     for (int r = 0; r < R; ++r) mbar_init(smem_u32(&mbar[g * R + r]), 1);
@@ -218,21 +247,37 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
 
   float* my_ring = ring + (size_t)g * R * SLOT;
   bool alive = true;
-  int issued = 0;
-  // item q = batch q - 1 (q = 0: the plane below the chunk, for the carries)
-  auto issue = [&](int q) {
-    if (q > nbatch || !alive) return;
-    issued = q + 1;
+  int issued = 0, waited = 0;
+  // issue cursor (tile, item), ahead of the consumer by up to R - 1 items
+  int is_t = blockIdx.x, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0;
+  auto issue_seek = [&]() {
+    if (is_t < ntiles) {
+      const TileGeom tg = tile_geom(is_t, nxb, ny, nz, L.nzc);
+      is_M = tile_items<ZC>(tg.zlen);
+      is_x0 = tg.x0;
+      is_yp = yneg ? tg.y + 1 : tg.y;  // lower padded row of the box
+      is_zp = tg.zbeg + zs;            // padded plane of B(zbeg - 1), shifted for sgn n^z < 0
+    }
+  };
+  issue_seek();
+  auto issue = [&]() -> bool {
+    if (is_t >= ntiles || !alive) return false;
+    const int slot = issued % R;
     __syncwarp();
     if (lane == 0) {
-      const int slot = q % R;
       const uint32_t bar = smem_u32(&mbar[g * R + slot]);
-      const int zp = (q == 0 ? zbeg - 1 : zbeg + (q - 1) * ZC) + zs + 1;  // padded plane
-      const int yp = yneg ? y + 1 : y;                                 // lower row (padded)
       fence_proxy_async();
       mbar_arrive_tx(bar, BOXX * DPT * 2 * ZC * 4);
-      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOT), &tmap, x0, i0, yp, zp, bar);
+      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOT), &tmap, is_x0, i0, is_yp,
+                  is_zp + is_m * ZC, bar);
     }
+    ++issued;
+    if (++is_m == is_M) {
+      is_m = 0;
+      is_t += gridDim.x;
+      issue_seek();
+    }
+    return true;
   };
   auto wait_item = [&](int q) -> bool {
     if (!alive || *abort_flag) {
@@ -244,158 +289,157 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       alive = false;
       return false;
     }
+    waited = q + 1;
     return true;
   };
   // element (plane j, row r, direction k) of a slot, at the lane's pair
-  const int wc = 2 + 2 * lane;  // window column of xa: x - (x0 - 2)
-  auto at = [&](const float* slot, int j, int r, int k) {
-    return slot + ((j * 2 + r) * DPT + k) * BOXX + wc;
-  };
+  const int wc = 2 + 2 * lane;  // window column of the pair's first site
 
-  for (int r = 0; r < R - 1; ++r) issue(r);
-
-  float2 carry[DPT];
-  {
-    issue(R - 1);
-    const bool ok = wait_item(0);
-    const float* slot = my_ring;
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) {
-      carry[k] = make_float2(0.f, 0.f);
-      if (ok) {
-        const float4 au = t.au[i0 + k];
-        const bool xneg = __float_as_int(au.w) & 1;
-        carry[k] = bilinear(at(slot, 0, row_own, k), at(slot, 0, row_up, k), xneg ? 2 : -1, xneg,
-                            f2s(au.x), f2s(-au.x), f2s(au.y), f2s(-au.y));
-      }
-    }
+  while (issued < R - 1 && issue()) {
   }
 
-  double bud_a = 0.0, bud_b = 0.0;
-  for (int b = 0; b < nbatch; ++b) {
-    const int q = b + 1;
-    const int zb = zbeg + b * ZC;
-    const int nb = min(ZC, zend - zb);
-    float2* part = part2 + (size_t)(b & 1) * G * ZC * 4 * 32;
-    // the lane's site coefficients, loaded now so that their latency
-    // overlaps the stream pass
-    float fka[ZC][2], fk0[ZC][2], flam[ZC][2], feta[ZC][2];
+  float2 carry[DPT];
 #pragma unroll
-    for (int j = 0; j < ZC; ++j) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const bool okx = (xa + h < nx) && (j < nb);
-        const long long st = okx ? ((long long)(zb + j) * ny + y) * nx + xa + h : 0;
-        fka[j][h] = fld(cf.ka, cf.ka_s, st);
-        fk0[j][h] = fld(cf.k0, cf.k0_s, st);
-        flam[j][h] = fld(cf.lam, cf.lam_s, st);
-        feta[j][h] = fld(cf.eta, cf.eta_s, st);
+  for (int k = 0; k < DPT; ++k) carry[k] = make_float2(0.f, 0.f);
+  float bud_a = 0.f, bud_b = 0.f;  // FP32 per batch, folded into FP64 below
+  double bud_da = 0.0, bud_db = 0.0;
+  int q = 0;  // items consumed
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const TileGeom tg = tile_geom(ti, nxb, ny, nz, L.nzc);
+    const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
+    const int M = tile_items<ZC>(tg.zlen);
+    const int xa = x0 + 2 * lane;  // the lane's pair (xa, xa + 1)
+    const bool in0 = xa < nx, in1 = xa + 1 < nx;
+    // x ghost columns this lane mirrors into (periodic x): column GL - 1
+    // holds x = nx - 1, column nx + GL holds x = 0
+    const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
+    const bool gx_hi = gr.periodic[0] && xa == 0;
+    const bool lo_from_y = xa + 1 == nx - 1;
+    const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
+    for (int m = 0; m < M; ++m, ++q) {
+      const int zb = zbeg - 1 + m * ZC;  // output plane of j = 0
+      // coefficient fields of this warp's first unit, loaded before the
+      // stream pass so that their latency overlaps it
+      float pka = 0.f, pk0 = 0.f, plam = 0.f, peta = 0.f;
+      if (g < nunits) {
+        const int j = g >> 1, x = x0 + ((g & 1) << 5) + lane, z = zb + j;
+        const bool v = x < nx && z >= zbeg && z < zend;
+        const long long st = v ? ((long long)z * ny + y) * nx + x : 0;
+        pka = fld(cf.ka, cf.ka_s, st);
+        pk0 = fld(cf.k0, cf.k0_s, st);
+        plam = fld(cf.lam, cf.lam_s, st);
+        peta = fld(cf.eta, cf.eta_s, st);
       }
-    }
-    issue(q + R - 1);
-    const bool ok = wait_item(q);
-    const float* slot = my_ring + (size_t)(q % R) * SLOT;
-    float2 Is[DPT][ZC];
-    float2 aE[ZC], aX[ZC], aY[ZC], aZ[ZC];
-#pragma unroll
-    for (int j = 0; j < ZC; ++j) aE[j] = aX[j] = aY[j] = aZ[j] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) {
-#pragma unroll
-      for (int j = 0; j < ZC; ++j) Is[k][j] = make_float2(0.f, 0.f);
-      if (ok) {
-        const float4 au = t.au[i0 + k];
-        const float4 nw = t.nw[i0 + k];
-        const int oct = __float_as_int(au.w);
-        const bool xneg = oct & 1;
-        const float2 ax = f2s(au.x), ay = f2s(au.y), nax = f2s(-au.x), nay = f2s(-au.y);
-        const float azw = zs ? 1.f - au.z : au.z;
-        const float2 az = f2s(azw), naz = f2s(-azw);
-        const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z);
-#pragma unroll
-        for (int j = 0; j < ZC; ++j) {
-          const float2 Bn = bilinear(at(slot, j, row_own, k), at(slot, j, row_up, k),
-                                     xneg ? 2 : -1, xneg, ax, nax, ay, nay);
-          // I* = (1 - a_z) B(z) + a_z B(z - sgn n^z): the carried plane is
-          // B(z - 1) for sgn = +1 and B(z) for sgn = -1
-          const float2 r = f2lerp(az, naz, carry[k], Bn);
-          carry[k] = Bn;
-          Is[k][j] = r;
-          aE[j] = f2add(aE[j], r);
-          aX[j] = f2fma(nx2, r, aX[j]);
-          aY[j] = f2fma(ny2, r, aY[j]);
-          aZ[j] = f2fma(nz2, r, aZ[j]);
-        }
+      while (issued < q + R && issue()) {
       }
-    }
+      const bool ok = wait_item(q);
+      float* slot = my_ring + (size_t)(q % R) * SLOT;
+      const float* own = slot + row_own * DPT * BOXX + wc;
+      const float* up = slot + row_up * DPT * BOXX + wc;
+      float2 Is[DPT][ZC];
+      float2 aE[ZC], aX[ZC], aY[ZC], aZ[ZC];
 #pragma unroll
-    for (int j = 0; j < ZC; ++j) {
-      float2* p = part + (((size_t)g * ZC + j) * 4) * 32 + lane;
-      p[0] = aE[j];
-      p[32] = aX[j];
-      p[64] = aY[j];
-      p[96] = aZ[j];
-    }
-    __syncthreads();
-    // every warp sums the G partials of its own lanes' sites and forms the
-    // collision scalars itself (no second barrier; the partials are double
-    // buffered across batches)
-    float2 al[ZC], c0[ZC], c1x[ZC], c1y[ZC], c1z[ZC];
-    float ea = 0.f, eb = 0.f;  // this batch's budget terms, folded into FP64 below
-#pragma unroll
-    for (int j = 0; j < ZC; ++j) {
-      float2 E = make_float2(0.f, 0.f), Fx = E, Fy = E, Fz = E;
-      for (int qq = 0; qq < G; ++qq) {
-        const float2* p = part + (((size_t)qq * ZC + j) * 4) * 32 + lane;
-        E = f2add(E, p[0]);
-        Fx = f2add(Fx, p[32]);
-        Fy = f2add(Fy, p[64]);
-        Fz = f2add(Fz, p[96]);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float Es = h ? E.y : E.x;
-        const Coef cc = collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, fka[j][h],
-                                        fk0[j][h], flam[j][h], feta[j][h], Es,
-                                        h ? Fx.y : Fx.x, h ? Fy.y : Fy.x, h ? Fz.y : Fz.x);
-        (h ? al[j].y : al[j].x) = cc.alpha;
-        (h ? c0[j].y : c0[j].x) = cc.c0;
-        (h ? c1x[j].y : c1x[j].x) = cc.c1x;
-        (h ? c1y[j].y : c1y[j].x) = cc.c1y;
-        (h ? c1z[j].y : c1z[j].x) = cc.c1z;
-        if (j < nb && xa + h < nx) {
-          ea += Es;
-          eb += cc.Enew;
-        }
-      }
-    }
-    if (L.budget_partials && g == 0) {
-      bud_a += (double)ea;
-      bud_b += (double)eb;
-    }
-    if (alive && in0) {
-      // x ghost columns this lane mirrors into (periodic x): column GL - 1
-      // holds x = nx - 1, column nx + GL holds x = 0
-      const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
-      const bool gx_hi = gr.periodic[0] && xa == 0;
-      const bool lo_from_y = xa + 1 == nx - 1;
-      const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
+      for (int j = 0; j < ZC; ++j) aE[j] = aX[j] = aY[j] = aZ[j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < DPT; ++k) {
-        const float4 nw = t.nw[i0 + k];
-        if (__float_as_int(t.au[i0 + k].w) & 8) continue;  // inert padding direction
-        const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z), w2 = f2s(nw.w);
+#pragma unroll
+        for (int j = 0; j < ZC; ++j) Is[k][j] = make_float2(0.f, 0.f);
+        if (ok) {
+          const float4 au = t.au[i0 + k];
+          const float4 nw = t.nw[i0 + k];
+          const bool xneg = __float_as_int(au.w) & 1;
+          const float2 ax = f2s(au.x), ay = f2s(au.y), nax = f2s(-au.x), nay = f2s(-au.y);
+          const float azw = zs ? 1.f - au.z : au.z;
+          const float2 az = f2s(azw), naz = f2s(-azw);
+          const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z);
+#pragma unroll
+          for (int j = 0; j < ZC; ++j) {
+            const int off = (j * 2 * DPT + k) * BOXX;
+            const float2 Bn = bilinear(own + off, up + off, xneg ? 2 : -1, xneg, ax, nax, ay, nay);
+            // I* = (1 - a_z) B(z) + a_z B(z - sgn n^z): the carried plane is
+            // B(z - 1) for sgn = +1 and B(z) for sgn = -1
+            const float2 r = f2lerp(az, naz, carry[k], Bn);
+            carry[k] = Bn;
+            Is[k][j] = r;
+            aE[j] = f2add(aE[j], r);
+            aX[j] = f2fma(nx2, r, aX[j]);
+            aY[j] = f2fma(ny2, r, aY[j]);
+            aZ[j] = f2fma(nz2, r, aZ[j]);
+          }
+        }
+      }
+      // the slot has been read: it now holds this warp's partial moments
+      // [ZC][E, Fx, Fy, Fz][64 sites]
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < ZC; ++j) {
+        float2* p = reinterpret_cast<float2*>(slot + j * 4 * 64) + lane;
+        p[0] = aE[j];
+        p[32] = aX[j];
+        p[64] = aY[j];
+        p[96] = aZ[j];
+      }
+      __syncthreads();
+      // coefficient units: unit u = (plane u / 2, sites 32 (u % 2) .. + 31)
+      for (int u = g; u < nunits; u += G) {
+        const int j = u >> 1, f = ((u & 1) << 5) + lane;
+        const int x = x0 + f, z = zb + j;
+        const bool v = x < nx && z >= zbeg && z < zend;
+        float ka = pka, k0 = pk0, lam = plam, eta = peta;
+        if (u != g) {
+          const long long st = v ? ((long long)z * ny + y) * nx + x : 0;
+          ka = fld(cf.ka, cf.ka_s, st);
+          k0 = fld(cf.k0, cf.k0_s, st);
+          lam = fld(cf.lam, cf.lam_s, st);
+          eta = fld(cf.eta, cf.eta_s, st);
+        }
+        const int s = q % R;
+        float E = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f;
+        for (int qq = 0; qq < G; ++qq) {
+          const float* p = ring + ((size_t)qq * R + s) * SLOT + j * 4 * 64 + f;
+          E += p[0];
+          Fx += p[64];
+          Fy += p[128];
+          Fz += p[192];
+        }
+        const Coef cc =
+            collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, ka, k0, lam, eta, E, Fx, Fy, Fz);
+        float* c = coef + j * 5 * 64 + f;
+        c[0] = cc.alpha;
+        c[64] = cc.c0;
+        c[128] = cc.c1x;
+        c[192] = cc.c1y;
+        c[256] = cc.c1z;
+        if (v) {
+          bud_a += E;
+          bud_b += cc.Enew;
+        }
+      }
+      __syncthreads();
+      if (L.budget_partials && g < nunits) {
+        bud_da += (double)bud_a;
+        bud_db += (double)bud_b;
+        bud_a = bud_b = 0.f;
+      }
+      if (alive && in0) {
 #pragma unroll
         for (int j = 0; j < ZC; ++j) {
-          if (j < nb) {
-            const int z = zb + j;
-            const float2 eq = f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j])));
-            const float2 o = f2fma(al[j], Is[k][j], f2mul(w2, eq));
+          const int z = zb + j;
+          if (z < zbeg || z >= zend) continue;
+          const float2* c = reinterpret_cast<const float2*>(coef + j * 5 * 64) + lane;
+          const float2 al = c[0], c0 = c[32], c1x = c[64], c1y = c[96], c1z = c[128];
+          const bool z_face = gr.periodic[2] && (z == 0 || z == nz - 1);
+          float* row = out + (long long)i0 * gr.si + (long long)(z + 1) * gr.sz +
+                       (long long)(y + 1) * gr.sy;
+#pragma unroll
+          for (int k = 0; k < DPT; ++k) {
+            if (__float_as_int(t.au[i0 + k].w) & 8) continue;  // inert padding direction
+            const float4 nw = t.nw[i0 + k];
+            const float2 eq = f2fma(f2s(nw.z), c1z, f2fma(f2s(nw.y), c1y, f2fma(f2s(nw.x), c1x, c0)));
+            const float2 o = f2fma(al, Is[k][j], f2mul(f2s(nw.w), eq));
             const float vlo = lo_from_y ? o.y : o.x;
-            const bool z_face = gr.periodic[2] && (z == 0 || z == nz - 1);
             if (!(y_face || z_face)) {
-              float* base = out + (long long)(i0 + k) * gr.si + (long long)(z + 1) * gr.sz +
-                            (long long)(y + 1) * gr.sy;
+              float* base = row + (long long)k * gr.si;
               if (in1) *reinterpret_cast<float2*>(base + xa + GL) = o;
               else base[xa + GL] = o.x;
               if (gx_lo) base[GL - 1] = vlo;
@@ -423,87 +467,161 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       }
     }
   }
-  // every issued copy must land before the CTA's shared memory is released
-  for (int qq = nbatch + 1; qq < issued; ++qq)
+  // copies still in flight (only after a failed wait) must land before the
+  // CTA's shared memory is released; each slot has at most one outstanding
+  for (int qq = waited; qq < issued; ++qq) {
     mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), L.err);
-  if (!alive) {
-    for (int qq = 0; qq < issued; ++qq)
-      mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), L.err);
   }
   if (L.budget_partials) {
     for (int s = 16; s > 0; s >>= 1) {
-      bud_a += __shfl_xor_sync(0xffffffffu, bud_a, s);
-      bud_b += __shfl_xor_sync(0xffffffffu, bud_b, s);
+      bud_da += __shfl_xor_sync(0xffffffffu, bud_da, s);
+      bud_db += __shfl_xor_sync(0xffffffffu, bud_db, s);
     }
-    if (lane == 0) {
-      const long long blk =
-          ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-      atomicAdd(L.budget_partials + 2 * blk, bud_a);
-      atomicAdd(L.budget_partials + 2 * blk + 1, bud_b);
+    if (lane == 0 && g < nunits) {
+      bsum[2 * g] = bud_da;
+      bsum[2 * g + 1] = bud_db;
+    }
+    __syncthreads();
+    if (g == 0 && lane == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < min(G, nunits); ++w) {
+        a += bsum[2 * w];
+        b += bsum[2 * w + 1];
+      }
+      atomicAdd(L.budget_partials + 2 * blockIdx.x, a);
+      atomicAdd(L.budget_partials + 2 * blockIdx.x + 1, b);
     }
   }
 }
 
 template <int DPT, int ZC, int R>
 size_t step_smem(int G) {
-  return sizeof(float) * (size_t)G * R * slot_floats<DPT, ZC>() +
-         sizeof(float2) * 32 * ((size_t)2 * G * ZC * 4) + 8 * (size_t)G * R + 16;
+  return sizeof(float) * ((size_t)G * R * slot_floats<DPT, ZC>() + ZC * 5 * 64) +
+         8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
 }
 
-template <int DPT, int ZC, int R, int MAXT>
-cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable& t, int zchunk,
-                       cudaStream_t s, int* nblocks) {
-  const int G = L.N / DPT;  // internal (padded) direction count / directions per warp
-  if (!L.tmap_in || G < 1 || G * DPT != L.N || 32 * G > MAXT) return cudaErrorInvalidValue;
-  dim3 block(32, G);
-  dim3 grid((L.g.nx + 63) / 64, L.g.ny, (L.g.nz + zchunk - 1) / zchunk);
-  const long long nb_ = (long long)grid.x * grid.y * grid.z;
-  if (L.budget_partials && nb_ > L.partials_cap) return cudaErrorInvalidValue;
-  if (nblocks) *nblocks = (int)nb_;
-  const size_t smem = step_smem<DPT, ZC, R>(G);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+template <int DPT, int ZC, int R, int MAXT, int MINB>
+cudaError_t set_smem_attr() {
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && !(attr_set >> dev & 1ull)) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_step_f32<DPT, ZC, R, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set |= 1ull << dev;
-  }
-  k_step_f32<DPT, ZC, R, MAXT><<<grid, block, smem, s>>>(*L.tmap_in, L, c, t, zchunk);
+  if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<DPT, ZC, R, MAXT, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+  if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
+  return e;
+}
+
+template <int DPT, int ZC, int R, int MAXT, int MINB>
+cudaError_t occupancy(int G, int* per_sm) {
+  cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, MINB>();
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_step_f32<DPT, ZC, R, MAXT, MINB>,
+                                                       32 * G, step_smem<DPT, ZC, R>(G));
+}
+
+template <int DPT, int ZC, int R, int MAXT, int MINB>
+cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
+                       cudaStream_t s, int* nblocks) {
+  const int G = L.N / DPT;  // internal (padded) direction count / directions per warp
+  if (!L.tmap_in || G < 1 || G * DPT != L.N || 32 * G > MAXT || L.nzc < 1 || L.nzc > L.g.nz ||
+      L.ctas < 1)
+    return cudaErrorInvalidValue;
+  if (L.budget_partials && L.ctas > L.partials_cap) return cudaErrorInvalidValue;
+  if (nblocks) *nblocks = L.ctas;
+  const size_t smem = step_smem<DPT, ZC, R>(G);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, MINB>();
+  if (e != cudaSuccess) return e;
+  k_step_f32<DPT, ZC, R, MAXT, MINB><<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, L, c, t);
   return cudaGetLastError();
 }
 
 constexpr int kRing = 2;
 
+// Dispatch over the compiled tile plans (directions per warp, planes per
+// batch, thread cap, CTAs per SM the register budget is sized for).
+#define LBRT_TILE_PLANS(X) \
+  X(5, 2, 320, 2)          \
+  X(10, 1, 640, 1)         \
+  X(8, 2, 512, 1)          \
+  X(4, 2, 512, 1)          \
+  X(4, 1, 768, 1)
+
 }  // namespace
 
-// Compiled tile plans (directions per warp, planes per batch, thread cap of
-// the launch bounds), in order of preference for the host's planner, which
-// also checks the shared-memory need with step_tile_smem().
-const int kTilePlans[][3] = {{5, 2, 512}, {10, 1, 640}, {8, 2, 512}, {4, 2, 512}, {4, 1, 768}};
-const int kNumTilePlans = 5;
+#define LBRT_PLAN_ROW(D, Z, T, B) {D, Z, T},
+const int kTilePlans[][3] = {LBRT_TILE_PLANS(LBRT_PLAN_ROW)};
+#undef LBRT_PLAN_ROW
+const int kNumTilePlans = sizeof(kTilePlans) / sizeof(kTilePlans[0]);
 
 size_t step_tile_smem(int dpt, int zc, int warps) {
-  if (dpt == 5 && zc == 2) return step_smem<5, 2, kRing>(warps);
-  if (dpt == 10 && zc == 1) return step_smem<10, 1, kRing>(warps);
-  if (dpt == 8 && zc == 2) return step_smem<8, 2, kRing>(warps);
-  if (dpt == 4 && zc == 2) return step_smem<4, 2, kRing>(warps);
-  if (dpt == 4 && zc == 1) return step_smem<4, 1, kRing>(warps);
+#define LBRT_SMEM(D, Z, T, B) \
+  if (dpt == D && zc == Z) return step_smem<D, Z, kRing>(warps);
+  LBRT_TILE_PLANS(LBRT_SMEM)
+#undef LBRT_SMEM
   return (size_t)-1;
 }
 
 cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                               int dpt, int zc, cudaStream_t s, int* nblocks) {
-  const int zchunk = 32;
-  if (dpt == 5 && zc == 2) return launch_f32<5, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
-  if (dpt == 10 && zc == 1) return launch_f32<10, 1, kRing, 640>(L, c, t, zchunk, s, nblocks);
-  if (dpt == 8 && zc == 2) return launch_f32<8, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
-  if (dpt == 4 && zc == 2) return launch_f32<4, 2, kRing, 512>(L, c, t, zchunk, s, nblocks);
-  if (dpt == 4 && zc == 1) return launch_f32<4, 1, kRing, 768>(L, c, t, zchunk, s, nblocks);
+#define LBRT_LAUNCH(D, Z, T, B) \
+  if (dpt == D && zc == Z) return launch_f32<D, Z, kRing, T, B>(L, c, t, s, nblocks);
+  LBRT_TILE_PLANS(LBRT_LAUNCH)
+#undef LBRT_LAUNCH
   return cudaErrorInvalidValue;
+}
+
+// Persistent grid of the static kernel: CTAs = resident CTAs per SM x SMs
+// (at most one per tile), and the number of z chunks nzc that minimises the
+// busiest CTA's share of plane loads under the round-robin tile order (each
+// tile loads zlen + 1 planes rounded up to whole batches, plus a small
+// per-tile overhead).
+cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int* nzc, int* ctas) {
+  const int G = Ni / dpt;
+  int per_sm = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define LBRT_OCC(D, Z, T, B) \
+  if (dpt == D && zc == Z) e = occupancy<D, Z, kRing, T, B>(G, &per_sm);
+  LBRT_TILE_PLANS(LBRT_OCC)
+#undef LBRT_OCC
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long slots = (long long)per_sm * sms;
+  const long long txy = (long long)((g.nx + 63) / 64) * g.ny;
+  double best = 1e300;
+  int best_c = 1;
+  const int cmax = std::min(g.nz, 64);
+  for (int c = 1; c <= cmax; ++c) {
+    const long long nt = txy * c;
+    if (nt > (1LL << 24)) break;
+    const long long nc = std::min(nt, slots);
+    const int base = g.nz / c, rem = g.nz % c;
+    auto cost = [&](long long ti) {
+      const long long ch = ti / txy;
+      const int zlen = base + (ch < rem ? 1 : 0);
+      return (double)((zlen + 1 + zc - 1) / zc * zc) + 0.5;
+    };
+    double worst = 0.0;  // the busiest CTA of the round-robin order
+    for (long long b = 0; b < nc; ++b) {
+      double sum = 0.0;
+      for (long long ti = b; ti < nt; ti += nc) sum += cost(ti);
+      worst = std::max(worst, sum);
+    }
+    if (worst < best * 0.999) {
+      best = worst;
+      best_c = c;
+    }
+  }
+  *nzc = best_c;
+  *ctas = (int)std::min<long long>(txy * best_c, slots);
+  return cudaSuccess;
 }
 
 bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int dpt, int zc,

@@ -17,6 +17,7 @@ struct lb_rt {
   int N = 0;                    // directions, external (user) order
   int Ni = 0;                   // internal directions including inert padding
   int dpt = 0, zc = 0;          // tile plan of the static kernel
+  int nzc = 0, ctas = 0;        // its persistent grid: z chunks, CTAs
   std::vector<int> ext_of_int;  // internal -> external index (-1: padding)
   std::vector<int> int_of_ext;  // external -> internal index
   int* d_int_of_ext = nullptr;  // device copy
@@ -362,6 +363,12 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
       }
     }
     h->tmap_ok = true;
+    e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, &h->nzc, &h->ctas);
+    if (e != cudaSuccess) {
+      g_create_msg = std::string("static kernel grid: ") + cudaGetErrorString(e);
+      lb_rt_destroy(h);
+      return LB_RT_ECUDA;
+    }
   }
   *out = h;
   return LB_RT_OK;
@@ -499,6 +506,8 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     L.N = h->Ni;
     L.dpt = h->dpt;
     L.zc = h->zc;
+    L.nzc = h->nzc;
+    L.ctas = h->ctas;
     L.dt = (float)h->dt;
     L.collision = h->cfg.collision;
     L.lambda_iters = h->cfg.lambda_iters;

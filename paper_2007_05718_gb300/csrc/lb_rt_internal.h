@@ -78,6 +78,7 @@ struct StepLaunch {
   Grid g;
   int N;               // internal direction count (padding included)
   int dpt, zc;         // tile plan of the static kernel: directions per warp, planes per batch
+  int nzc, ctas;       // static kernel: z chunks per column, CTAs of the persistent grid
   float dt;
   int collision;       // LB_RT_IMPLICIT_EXACT / LB_RT_EXPLICIT / LB_RT_LAMBDA_K
   int lambda_iters;
@@ -120,6 +121,9 @@ bool make_pop_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, in
 extern const int kTilePlans[][3];
 extern const int kNumTilePlans;
 size_t step_tile_smem(int dpt, int zc, int warps);
+// z chunks and CTA count of the static kernel's persistent grid for this
+// grid and plan on the current device (occupancy query).
+cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int* nzc, int* ctas);
 
 // Message returned by lb_rt_last_error(NULL) on this thread (calls without a handle).
 void set_unbound_error(const std::string& m);
