@@ -41,12 +41,9 @@ namespace {
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
-// t a + (1 - t) b as two fused multiply-adds, with nt = -t precomputed
-__device__ __forceinline__ float2 f2lerp(float2 t, float2 nt, float2 a, float2 b) {
-  return __ffma2_rn(t, a, __ffma2_rn(nt, b, b));
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
-
 // ---- mbarrier and TMA ------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -121,6 +118,8 @@ struct Coef {
 //     table a pass maps (E, F) -> (A (E* + dt eta + dt k0 E), A (F* + dt k0 lam F / d)),
 //     and the output populations are those of pass K, built from the
 //     moments of pass K - 1.
+// The quotients use the fast division (a few ulp): every denominator is at
+// least 1 for non-negative opacities and lam <= d.
 __device__ __forceinline__ Coef collide_scalars(int mode, int iters, float dt, float inv_d,
                                                 float ka, float k0, float lam, float eta,
                                                 float Es, float Fx, float Fy, float Fz) {
@@ -133,7 +132,7 @@ __device__ __forceinline__ Coef collide_scalars(int mode, int iters, float dt, f
     c.c1x = g * Fx; c.c1y = g * Fy; c.c1z = g * Fz;
     return c;
   }
-  const float A = 1.f / (1.f + dt * (k0 + ka));
+  const float A = __fdividef(1.f, 1.f + dt * (k0 + ka));
   float gx, gy, gz;
   if (mode == LB_RT_LAMBDA_K) {
     float E = Es;
@@ -146,8 +145,8 @@ __device__ __forceinline__ Coef collide_scalars(int mode, int iters, float dt, f
     c.c0 = A * dt * (eta + k0 * E);
     c.Enew = fmaf(A, Es, c.c0);
   } else {
-    const float E = (Es + dt * eta) / (1.f + dt * ka);
-    const float r = 1.f / (1.f + dt * (ka + k0) - dt * k0 * lam * inv_d);
+    const float E = __fdividef(Es + dt * eta, 1.f + dt * ka);
+    const float r = __fdividef(1.f, 1.f + dt * (ka + k0) - dt * k0 * lam * inv_d);
     gx = Fx * r; gy = Fy * r; gz = Fz * r;
     c.c0 = fmaf(-A, Es, E);
     c.Enew = E;
@@ -161,19 +160,6 @@ __device__ __forceinline__ Coef collide_scalars(int mode, int iters, float dt, f
 template <int DPT, int ZC>
 __host__ __device__ constexpr int slot_floats() {
   return ((BOXX * DPT * 2 * ZC * 4 + 127) / 128) * 32;  // 128-byte aligned slots
-}
-
-// In-plane bilinear value of the lane's pair from one box row pair: r0 the
-// own row, r1 the upwind row (pointers at the window column of the pair),
-// upwind column at offset `du` (-1 or +2) from the pair's first site.
-__device__ __forceinline__ float2 bilinear(const float* r0, const float* r1, int du, bool xneg,
-                                           float2 ax, float2 nax, float2 ay, float2 nay) {
-  const float2 v0 = *reinterpret_cast<const float2*>(r0);
-  const float2 v1 = *reinterpret_cast<const float2*>(r1);
-  const float u0 = r0[du], u1 = r1[du];
-  const float2 w0 = xneg ? make_float2(v0.y, u0) : make_float2(u0, v0.x);
-  const float2 w1 = xneg ? make_float2(v1.y, u1) : make_float2(u1, v1.x);
-  return f2lerp(ay, nay, f2lerp(ax, nax, w1, v1), f2lerp(ax, nax, w0, v0));
 }
 
 // Tile schedule of the persistent grid: tile ti covers the 64 columns
@@ -207,8 +193,19 @@ __device__ __forceinline__ int tile_items(int zlen) {
   return (zlen + 1 + ZC - 1) / ZC;
 }
 
-template <int DPT, int ZC, int R, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB)
+// Per-direction constants in shared memory, as pre-broadcast pairs for the
+// packed float32 x 2 arithmetic: s0 = (a_x, a_x, a_y, a_y), s1 = (a_z', a_z',
+// n_x, n_x), s2 = (n_y, n_y, n_z, n_z) for the stream pass (a_z' the weight of
+// the carried plane), o0 = (w, w, w n_x, w n_x), o1 = (w n_y, w n_y, w n_z,
+// w n_z) for the output; sh = offset (floats) of the x-upwind pair of the
+// lane's own pair (-1 for sgn n^x = +1, +1 otherwise); inert = padding entry.
+struct DirConst {
+  float4 s0, s1, s2, o0, o1;
+  int sh, inert, pad0, pad1;
+};
+
+template <int DPT, int ZC, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const StaticCoef cf,
            const DirTable t) {
   constexpr int SLOT = slot_floats<DPT, ZC>();
@@ -218,11 +215,12 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   const int lane = threadIdx.x, g = threadIdx.y;
   const Grid& gr = L.g;
   const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
-  // shared layout: ring [G][R][SLOT] | coef [ZC][5][64] | mbar [G][R] |
-  // budget [2 ZC][2] double | abort flag
+  // shared layout: ring [G][R][SLOT] | coef [ZC][5][64] | dirs [N] DirConst |
+  // mbar [G][R] | budget [2 ZC][2] double | abort flag
   float* ring = reinterpret_cast<float*>(smem_raw);
   float* coef = ring + (size_t)G * R * SLOT;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(coef + ZC * 5 * 64);
+  DirConst* dirs = reinterpret_cast<DirConst*>(coef + ZC * 5 * 64);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(dirs + G * DPT);
   double* bsum = reinterpret_cast<double*>(mbar + G * R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 4 * ZC);
 
@@ -238,12 +236,31 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   const int row_own = yneg ? 0 : 1, row_up = yneg ? 1 : 0;
   const int nunits = 2 * ZC;  // coefficient units: (plane, half row) pairs of a batch
 
+  for (int i = g * 32 + lane; i < G * DPT; i += G * 32) {
+    const float4 au = t.au[i], nw = t.nw[i];
+    const int oct = __float_as_int(au.w);
+    const float azw = (oct & 4) ? 1.f - au.z : au.z;
+    DirConst d;
+    d.s0 = make_float4(au.x, au.x, au.y, au.y);
+    d.s1 = make_float4(azw, azw, nw.x, nw.x);
+    d.s2 = make_float4(nw.y, nw.y, nw.z, nw.z);
+    const float wx = nw.w * nw.x, wy = nw.w * nw.y, wz = nw.w * nw.z;
+    d.o0 = make_float4(nw.w, nw.w, wx, wx);
+    d.o1 = make_float4(wy, wy, wz, wz);
+    d.sh = (oct & 1) ? 1 : -1;
+    d.inert = oct & 8;
+    d.pad0 = d.pad1 = 0;
+    dirs[i] = d;
+  }
   if (lane == 0) {
     for (int r = 0; r < R; ++r) mbar_init(smem_u32(&mbar[g * R + r]), 1);
   }
   if (g == 0 && lane == 0) *abort_flag = 0;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
+  unsigned inert_mask = 0;  // padding directions of this warp
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) inert_mask |= dirs[i0 + k].inert ? 1u << k : 0u;
 
   float* my_ring = ring + (size_t)g * R * SLOT;
   bool alive = true;
@@ -292,8 +309,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
     waited = q + 1;
     return true;
   };
-  // element (plane j, row r, direction k) of a slot, at the lane's pair
-  const int wc = 2 + 2 * lane;  // window column of the pair's first site
+  const int wc = 2 + 2 * lane;  // window column of the lane's pair in a box row
 
   while (issued < R - 1 && issue()) {
   }
@@ -316,6 +332,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
     const bool gx_hi = gr.periodic[0] && xa == 0;
     const bool lo_from_y = xa + 1 == nx - 1;
     const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
+    float* const orow = out + (long long)i0 * gr.si + (long long)(y + 1) * gr.sy + xa + GL;
     for (int m = 0; m < M; ++m, ++q) {
       const int zb = zbeg - 1 + m * ZC;  // output plane of j = 0
       // coefficient fields of this warp's first unit, loaded before the
@@ -332,7 +349,9 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       }
       while (issued < q + R && issue()) {
       }
-      const bool ok = wait_item(q);
+      // after a failed wait the slot holds stale (finite, in-bounds) data:
+      // the pass runs anyway and the error word reports the step as failed
+      wait_item(q);
       float* slot = my_ring + (size_t)(q % R) * SLOT;
       const float* own = slot + row_own * DPT * BOXX + wc;
       const float* up = slot + row_up * DPT * BOXX + wc;
@@ -342,30 +361,33 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       for (int j = 0; j < ZC; ++j) aE[j] = aX[j] = aY[j] = aZ[j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < DPT; ++k) {
+        const DirConst& d = dirs[i0 + k];
+        const float4 s0 = d.s0, s1 = d.s1, s2 = d.s2;
+        const float2 ax = make_float2(s0.x, s0.y), ay = make_float2(s0.z, s0.w);
+        const float2 az = make_float2(s1.x, s1.y), nx2 = make_float2(s1.z, s1.w);
+        const float2 ny2 = make_float2(s2.x, s2.y), nz2 = make_float2(s2.z, s2.w);
+        const float* ownS = own + d.sh;
+        const float* upS = up + d.sh;
 #pragma unroll
-        for (int j = 0; j < ZC; ++j) Is[k][j] = make_float2(0.f, 0.f);
-        if (ok) {
-          const float4 au = t.au[i0 + k];
-          const float4 nw = t.nw[i0 + k];
-          const bool xneg = __float_as_int(au.w) & 1;
-          const float2 ax = f2s(au.x), ay = f2s(au.y), nax = f2s(-au.x), nay = f2s(-au.y);
-          const float azw = zs ? 1.f - au.z : au.z;
-          const float2 az = f2s(azw), naz = f2s(-azw);
-          const float2 nx2 = f2s(nw.x), ny2 = f2s(nw.y), nz2 = f2s(nw.z);
-#pragma unroll
-          for (int j = 0; j < ZC; ++j) {
-            const int off = (j * 2 * DPT + k) * BOXX;
-            const float2 Bn = bilinear(own + off, up + off, xneg ? 2 : -1, xneg, ax, nax, ay, nay);
-            // I* = (1 - a_z) B(z) + a_z B(z - sgn n^z): the carried plane is
-            // B(z - 1) for sgn = +1 and B(z) for sgn = -1
-            const float2 r = f2lerp(az, naz, carry[k], Bn);
-            carry[k] = Bn;
-            Is[k][j] = r;
-            aE[j] = f2add(aE[j], r);
-            aX[j] = f2fma(nx2, r, aX[j]);
-            aY[j] = f2fma(ny2, r, aY[j]);
-            aZ[j] = f2fma(nz2, r, aZ[j]);
-          }
+        for (int j = 0; j < ZC; ++j) {
+          const int off = (j * 2 * DPT + k) * BOXX;
+          // Eq. (interp) as nested lerps: x on both rows, then y, then z
+          // against the carried plane (B(z - 1) for sgn n^z = +1, B(z + 1)
+          // otherwise, the box being shifted by one plane for the latter)
+          const float2 P0 = *reinterpret_cast<const float2*>(own + off);
+          const float2 S0 = make_float2(ownS[off], ownS[off + 1]);
+          const float2 P1 = *reinterpret_cast<const float2*>(up + off);
+          const float2 S1 = make_float2(upS[off], upS[off + 1]);
+          const float2 X0 = f2fma(ax, f2sub(S0, P0), P0);
+          const float2 X1 = f2fma(ax, f2sub(S1, P1), P1);
+          const float2 Bn = f2fma(ay, f2sub(X1, X0), X0);
+          const float2 r = f2fma(az, f2sub(carry[k], Bn), Bn);
+          carry[k] = Bn;
+          Is[k][j] = r;
+          aE[j] = f2add(aE[j], r);
+          aX[j] = f2fma(nx2, r, aX[j]);
+          aY[j] = f2fma(ny2, r, aY[j]);
+          aZ[j] = f2fma(nz2, r, aZ[j]);
         }
       }
       // the slot has been read: it now holds this warp's partial moments
@@ -421,29 +443,68 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
         bud_db += (double)bud_b;
         bud_a = bud_b = 0.f;
       }
-      if (alive && in0) {
+      // I_i^{n+1} = alpha I*_i + w_i c0 + (w_i n_i) . c1, direction-major so
+      // that each direction's constants are read once per batch
+      float2 al[ZC], c0[ZC], c1x[ZC], c1y[ZC], c1z[ZC];
 #pragma unroll
-        for (int j = 0; j < ZC; ++j) {
-          const int z = zb + j;
-          if (z < zbeg || z >= zend) continue;
-          const float2* c = reinterpret_cast<const float2*>(coef + j * 5 * 64) + lane;
-          const float2 al = c[0], c0 = c[32], c1x = c[64], c1y = c[96], c1z = c[128];
-          const bool z_face = gr.periodic[2] && (z == 0 || z == nz - 1);
-          float* row = out + (long long)i0 * gr.si + (long long)(z + 1) * gr.sz +
-                       (long long)(y + 1) * gr.sy;
+      for (int j = 0; j < ZC; ++j) {
+        const float2* c = reinterpret_cast<const float2*>(coef + j * 5 * 64) + lane;
+        al[j] = c[0];
+        c0[j] = c[32];
+        c1x[j] = c[64];
+        c1y[j] = c[96];
+        c1z[j] = c[128];
+      }
+      bool zok[ZC], zface[ZC];
+      bool batch_plain = !y_face;
 #pragma unroll
-          for (int k = 0; k < DPT; ++k) {
-            if (__float_as_int(t.au[i0 + k].w) & 8) continue;  // inert padding direction
-            const float4 nw = t.nw[i0 + k];
-            const float2 eq = f2fma(f2s(nw.z), c1z, f2fma(f2s(nw.y), c1y, f2fma(f2s(nw.x), c1x, c0)));
-            const float2 o = f2fma(al, Is[k][j], f2mul(f2s(nw.w), eq));
+      for (int j = 0; j < ZC; ++j) {
+        const int z = zb + j;
+        zok[j] = z >= zbeg && z < zend;
+        zface[j] = gr.periodic[2] && (z == 0 || z == nz - 1);
+        batch_plain = batch_plain && zok[j] && !zface[j];
+      }
+      // fast path: every plane of the batch in the tile, no periodic-face
+      // images, every lane a full interior pair
+      const bool fast = __all_sync(0xffffffffu, in0 && in1 && !gx_lo && !gx_hi) && batch_plain;
+      if (alive && fast) {
+        float* base = orow + (long long)(zb + 1) * gr.sz;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          if (inert_mask >> k & 1u) continue;  // padding direction: its populations stay 0
+          const DirConst& d = dirs[i0 + k];
+          const float4 o0 = d.o0, o1 = d.o1;
+          const float2 w2 = make_float2(o0.x, o0.y), wx2 = make_float2(o0.z, o0.w);
+          const float2 wy2 = make_float2(o1.x, o1.y), wz2 = make_float2(o1.z, o1.w);
+#pragma unroll
+          for (int j = 0; j < ZC; ++j) {
+            const float2 eq =
+                f2fma(wz2, c1z[j], f2fma(wy2, c1y[j], f2fma(wx2, c1x[j], f2mul(w2, c0[j]))));
+            *reinterpret_cast<float2*>(base + (long long)k * gr.si + (long long)j * gr.sz) =
+                f2fma(al[j], Is[k][j], eq);
+          }
+        }
+      } else if (alive && in0) {
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          if (inert_mask >> k & 1u) continue;
+          const DirConst& d = dirs[i0 + k];
+          const float4 o0 = d.o0, o1 = d.o1;
+          const float2 w2 = make_float2(o0.x, o0.y), wx2 = make_float2(o0.z, o0.w);
+          const float2 wy2 = make_float2(o1.x, o1.y), wz2 = make_float2(o1.z, o1.w);
+#pragma unroll
+          for (int j = 0; j < ZC; ++j) {
+            if (!zok[j]) continue;
+            const int z = zb + j;
+            const float2 eq = f2fma(wz2, c1z[j], f2fma(wy2, c1y[j], f2fma(wx2, c1x[j], f2mul(w2, c0[j]))));
+            const float2 o = f2fma(al[j], Is[k][j], eq);
             const float vlo = lo_from_y ? o.y : o.x;
-            if (!(y_face || z_face)) {
-              float* base = row + (long long)k * gr.si;
-              if (in1) *reinterpret_cast<float2*>(base + xa + GL) = o;
-              else base[xa + GL] = o.x;
-              if (gx_lo) base[GL - 1] = vlo;
-              if (gx_hi) base[nx + GL] = o.x;
+            if (!(y_face || zface[j])) {
+              float* base = orow + (long long)k * gr.si + (long long)(z + 1) * gr.sz;
+              if (in1) *reinterpret_cast<float2*>(base) = o;
+              else base[0] = o.x;
+              if (gx_lo) base[GL - 1 - (xa + GL)] = vlo;
+              if (gx_hi) base[nx + GL - (xa + GL)] = o.x;
             } else {
               // a row or plane on a periodic face: every (row, plane) image
               const int rows[3] = {y + 1, (gr.periodic[1] && y == ny - 1) ? 0 : -1,
@@ -497,32 +558,32 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
 template <int DPT, int ZC, int R>
 size_t step_smem(int G) {
   return sizeof(float) * ((size_t)G * R * slot_floats<DPT, ZC>() + ZC * 5 * 64) +
-         8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
+         sizeof(DirConst) * (size_t)G * DPT + 8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
 }
 
-template <int DPT, int ZC, int R, int MAXT, int MINB>
+template <int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr() {
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<DPT, ZC, R, MAXT, MINB>,
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<DPT, ZC, R, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
   return e;
 }
 
-template <int DPT, int ZC, int R, int MAXT, int MINB>
+template <int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy(int G, int* per_sm) {
-  cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, MINB>();
+  cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_step_f32<DPT, ZC, R, MAXT, MINB>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_step_f32<DPT, ZC, R, MAXT, REGS>,
                                                        32 * G, step_smem<DPT, ZC, R>(G));
 }
 
-template <int DPT, int ZC, int R, int MAXT, int MINB>
+template <int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                        cudaStream_t s, int* nblocks) {
   const int G = L.N / DPT;  // internal (padded) direction count / directions per warp
@@ -533,22 +594,27 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   if (nblocks) *nblocks = L.ctas;
   const size_t smem = step_smem<DPT, ZC, R>(G);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, MINB>();
+  const cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
-  k_step_f32<DPT, ZC, R, MAXT, MINB><<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, L, c, t);
+  k_step_f32<DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, L, c, t);
   return cudaGetLastError();
 }
 
 constexpr int kRing = 2;
 
 // Dispatch over the compiled tile plans (directions per warp, planes per
-// batch, thread cap, CTAs per SM the register budget is sized for).
+// batch, thread cap, registers per thread), in order of preference.  A
+// scheduler holds floor(16384 / (32 x registers)) warps: 96 registers allow
+// 5 warps per scheduler (two CTAs of 9 warps, ico42 with 45 internal
+// directions, or one of 17), 128 allow 4 (one CTA of 16 warps: ico162 with 176
+// internal directions at 11 per warp).
 #define LBRT_TILE_PLANS(X) \
-  X(5, 2, 320, 2)          \
-  X(10, 1, 640, 1)         \
-  X(8, 2, 512, 1)          \
-  X(4, 2, 512, 1)          \
-  X(4, 1, 768, 1)
+  X(5, 2, 320, 96)         \
+  X(11, 1, 512, 128)       \
+  X(10, 1, 544, 96)        \
+  X(8, 2, 512, 128)        \
+  X(4, 2, 512, 128)        \
+  X(4, 1, 640, 96)
 
 }  // namespace
 

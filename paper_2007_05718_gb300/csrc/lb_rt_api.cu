@@ -148,7 +148,10 @@ void plan_directions(lb_rt* h) {
       std::stable_sort(c.begin(), c.end(), [&](int a, int b) {
         return (h->n[3 * a] < 0) < (h->n[3 * b] < 0);
       });
-    int best = -1, best_ni = 1 << 30;
+    // the first plan (in the kernel's order of preference) that fits and
+    // pads the direction set by at most 4 % more than the tightest plan
+    std::vector<int> ni_of(kNumTilePlans, -1);
+    int min_ni = 1 << 30;
     for (int p = 0; p < kNumTilePlans; ++p) {
       const int dpt = kTilePlans[p][0], zc = kTilePlans[p][1];
       if (zc > 1 && zc > h->grid.nz) continue;
@@ -157,11 +160,12 @@ void plan_directions(lb_rt* h) {
       const int warps = ni / dpt;
       if (ni > kMaxInternalDirs || 32 * warps > kTilePlans[p][2]) continue;
       if (step_tile_smem(dpt, zc, warps) > 227 * 1024) continue;
-      if (ni < best_ni) {
-        best = p;
-        best_ni = ni;
-      }
+      ni_of[p] = ni;
+      min_ni = std::min(min_ni, ni);
     }
+    int best = -1;
+    for (int p = 0; p < kNumTilePlans && best < 0; ++p)
+      if (ni_of[p] >= 0 && ni_of[p] * 100 <= min_ni * 104) best = p;
     h->dpt = best >= 0 ? kTilePlans[best][0] : 0;
     h->zc = best >= 0 ? kTilePlans[best][1] : 0;
     for (auto& c : cls) {
