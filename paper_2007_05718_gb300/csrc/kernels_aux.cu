@@ -190,40 +190,255 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// ---- 16-bit storage: f_i = I_i / w_i = E^ (1 + q_i), E^ = max(E, 1e-30) --
+
+constexpr float EPS_E = 1e-30f;
+
+__device__ __forceinline__ long long eidx(const Grid& g, int z, int y, int x) {
+  return (long long)(z + 1) * g.PX * g.PY + (long long)(y + 1) * g.PX + x + GL;
+}
+
+template <class ST> __device__ __forceinline__ float to_f(ST v);
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <class ST> __device__ __forceinline__ ST from_f(float v);
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// E^ of a site and every periodic mirror.
+__device__ __forceinline__ void store_e_site(float* e, const Grid& g, int z, int y, int x, float v) {
+  int xs[3], ys[3], zs[3];
+  const int nxs = mirrors(x, g.nx, g.periodic[0], GL, xs);
+  const int nys = mirrors(y, g.ny, g.periodic[1], 1, ys);
+  const int nzs = mirrors(z, g.nz, g.periodic[2], 1, zs);
+  for (int a = 0; a < nzs; ++a)
+    for (int b = 0; b < nys; ++b)
+      for (int c = 0; c < nxs; ++c)
+        e[(long long)zs[a] * g.PX * g.PY + (long long)ys[b] * g.PX + xs[c]] = v;
+}
+
+// Encode f_i (per internal direction, from `kind` and `data` as in
+// k_init_state) into q_i and E^.  Inert padding directions keep q = 0.
+template <class ST>
+__global__ void k_init_state16(Grid g, int Ni, int Next, const int* __restrict__ int_of_ext,
+                               const float* __restrict__ data, int kind, ST* __restrict__ pop,
+                               float* __restrict__ e, DirTable t) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.sites) return;
+  int x, y, z;
+  site_xyz(g, s, x, y, z);
+  const float d = (float)g.dims;
+  // f_i of internal direction i; E = sum_i w_i f_i
+  auto f_of = [&](int i) -> float {
+    const float4 nw = t.nw[i];
+    if (kind == LB_RT_STATE_ISOTROPIC) return data[s];
+    return data[s] + d * (nw.x * data[g.sites + s] + nw.y * data[2 * g.sites + s] +
+                          nw.z * data[3 * g.sites + s]);
+  };
+  float E = 0.f;
+  if (kind == LB_RT_STATE_POPULATIONS) {
+    for (int ex = 0; ex < Next; ++ex) E += data[(size_t)ex * g.sites + s];
+  } else if (kind == LB_RT_STATE_ISOTROPIC) {
+    E = data[s];
+  } else {
+    for (int i = 0; i < Ni; ++i) E = fmaf(t.nw[i].w, f_of(i), E);
+  }
+  const float Eh = fmaxf(E, EPS_E);
+  const float ri = 1.f / Eh;
+  store_e_site(e, g, z, y, x, Eh);
+  if (kind == LB_RT_STATE_POPULATIONS) {
+    for (int ex = 0; ex < Next; ++ex) {
+      const int i = int_of_ext[ex];
+      const float f = data[(size_t)ex * g.sites + s] / t.nw[i].w;
+      store_pop(pop, g, i, z, y, x, from_f<ST>(fmaf(f, ri, -1.f)));
+    }
+    return;
+  }
+  for (int i = 0; i < Ni; ++i) {
+    const bool inert = __float_as_int(t.au[i].w) & 8;
+    store_pop(pop, g, i, z, y, x, from_f<ST>(inert ? 0.f : fmaf(f_of(i), ri, -1.f)));
+  }
+}
+
+template <class ST>
+__device__ __forceinline__ float f_at(const ST* pop, const float* e, const Grid& g, int i, int z,
+                                      int y, int x) {
+  const float Eh = e[eidx(g, z, y, x)];
+  return fmaf(Eh, to_f<ST>(pop[pidx(g, i, z, y, x)]), Eh);
+}
+
+template <class ST>
+__global__ void k_moments16(Grid g, int N, const ST* __restrict__ pop, const float* __restrict__ e,
+                            float* __restrict__ E, float* __restrict__ F, float* __restrict__ P,
+                            DirTable t) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.sites) return;
+  int x, y, z;
+  site_xyz(g, s, x, y, z);
+  const float Eh = e[eidx(g, z, y, x)];
+  float es = 0, fx = 0, fy = 0, fz = 0, pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
+  for (int i = 0; i < N; ++i) {
+    const float4 nw = t.nw[i];
+    const float v = nw.w * fmaf(Eh, to_f<ST>(pop[pidx(g, i, z, y, x)]), Eh);
+    es += v;
+    fx = fmaf(nw.x, v, fx);
+    fy = fmaf(nw.y, v, fy);
+    fz = fmaf(nw.z, v, fz);
+    pxx = fmaf(nw.x * nw.x, v, pxx);
+    pxy = fmaf(nw.x * nw.y, v, pxy);
+    pxz = fmaf(nw.x * nw.z, v, pxz);
+    pyy = fmaf(nw.y * nw.y, v, pyy);
+    pyz = fmaf(nw.y * nw.z, v, pyz);
+    pzz = fmaf(nw.z * nw.z, v, pzz);
+  }
+  if (E) E[s] = es;
+  if (F) {
+    F[s] = fx;
+    F[g.sites + s] = fy;
+    F[2 * g.sites + s] = fz;
+  }
+  if (P) {
+    P[s] = pxx;
+    P[g.sites + s] = pxy;
+    P[2 * g.sites + s] = pxz;
+    P[3 * g.sites + s] = pyy;
+    P[4 * g.sites + s] = pyz;
+    P[5 * g.sites + s] = pzz;
+  }
+}
+
+template <class ST>
+__global__ void k_decode16(Grid g, int Next, const int* __restrict__ int_of_ext,
+                           const ST* __restrict__ pop, const float* __restrict__ e,
+                           float* __restrict__ out, DirTable t) {
+  const long long total = g.sites * (long long)Next;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int ex = (int)(k / g.sites);
+    int x, y, z;
+    site_xyz(g, k % g.sites, x, y, z);
+    const int i = int_of_ext[ex];
+    out[k] = t.nw[i].w * f_at(pop, e, g, i, z, y, x);
+  }
+}
+
+// Frozen cells in 16-bit storage: the site's E^ becomes the sum of the
+// prescribed values and every direction is re-encoded against it.
+template <class ST>
+__global__ void k_frozen16(Grid g, int Ni, int Next, const int* __restrict__ int_of_ext, int ncells,
+                           const int64_t* __restrict__ cells, const float* __restrict__ vals,
+                           ST* __restrict__ pop, float* __restrict__ e, double* injection,
+                           DirTable t) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  int x, y, z;
+  site_xyz(g, cells[c], x, y, z);
+  double old = 0.0, neu = 0.0;
+  for (int i = 0; i < Ni; ++i) old += (double)(t.nw[i].w * f_at(pop, e, g, i, z, y, x));
+  float E = 0.f;
+  for (int ex = 0; ex < Next; ++ex) {
+    E += vals[(size_t)c * Next + ex];
+    neu += (double)vals[(size_t)c * Next + ex];
+  }
+  const float Eh = fmaxf(E, EPS_E);
+  const float ri = 1.f / Eh;
+  for (int ex = 0; ex < Next; ++ex) {
+    const int i = int_of_ext[ex];
+    const float f = vals[(size_t)c * Next + ex] / t.nw[i].w;
+    store_pop(pop, g, i, z, y, x, from_f<ST>(fmaf(f, ri, -1.f)));
+  }
+  store_e_site(e, g, z, y, x, Eh);
+  if (injection) atomicAdd(injection, neu - old);
+}
+
+template <class ST>
+__global__ void k_total_partials16(Grid g, int N, const ST* __restrict__ pop,
+                                   const float* __restrict__ e, double* __restrict__ partials,
+                                   DirTable t) {
+  __shared__ double sh[BLK];
+  double acc = 0.0;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.sites;
+       s += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    site_xyz(g, s, x, y, z);
+    float v = 0.f;
+    for (int i = 0; i < N; ++i) v = fmaf(t.nw[i].w, f_at(pop, e, g, i, z, y, x), v);
+    acc += (double)v;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
 unsigned grid1d(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 
 }  // namespace
 
 cudaError_t launch_init_state(const Grid& g, int Ni, int Next, const int* int_of_ext,
-                              const float* data, int kind, void* pop, int storage,
+                              const float* data, int kind, void* pop, float* e, int storage,
                               const DirTable& t, cudaStream_t s) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
-  k_init_state<<<grid1d(g.sites), BLK, 0, s>>>(g, Ni, Next, int_of_ext, data, kind,
-                                               static_cast<float*>(pop), t);
+  if (storage == ST_F32)
+    k_init_state<<<grid1d(g.sites), BLK, 0, s>>>(g, Ni, Next, int_of_ext, data, kind,
+                                                 static_cast<float*>(pop), t);
+  else if (storage == ST_F16)
+    k_init_state16<__half><<<grid1d(g.sites), BLK, 0, s>>>(g, Ni, Next, int_of_ext, data, kind,
+                                                           static_cast<__half*>(pop), e, t);
+  else
+    k_init_state16<__nv_bfloat16><<<grid1d(g.sites), BLK, 0, s>>>(
+        g, Ni, Next, int_of_ext, data, kind, static_cast<__nv_bfloat16*>(pop), e, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const Grid& g, int N, const void* pop, int storage, const DirTable& t,
-                           float* E, float* F, float* P, cudaStream_t s) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
-  k_moments<<<grid1d(g.sites), BLK, 0, s>>>(g, N, pop, E, F, P, t);
+cudaError_t launch_moments(const Grid& g, int N, const void* pop, const float* e, int storage,
+                           const DirTable& t, float* E, float* F, float* P, cudaStream_t s) {
+  if (storage == ST_F32)
+    k_moments<<<grid1d(g.sites), BLK, 0, s>>>(g, N, pop, E, F, P, t);
+  else if (storage == ST_F16)
+    k_moments16<__half><<<grid1d(g.sites), BLK, 0, s>>>(g, N, static_cast<const __half*>(pop), e,
+                                                        E, F, P, t);
+  else
+    k_moments16<__nv_bfloat16><<<grid1d(g.sites), BLK, 0, s>>>(
+        g, N, static_cast<const __nv_bfloat16*>(pop), e, E, F, P, t);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const Grid& g, int Next, const int* int_of_ext, const void* pop,
-                          int storage, float* out, cudaStream_t s) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
-  k_decode<<<1024, BLK, 0, s>>>(g, Next, int_of_ext, pop, out);
+                          const float* e, int storage, const DirTable& t, float* out,
+                          cudaStream_t s) {
+  if (storage == ST_F32)
+    k_decode<<<1024, BLK, 0, s>>>(g, Next, int_of_ext, pop, out);
+  else if (storage == ST_F16)
+    k_decode16<__half><<<1024, BLK, 0, s>>>(g, Next, int_of_ext, static_cast<const __half*>(pop),
+                                            e, out, t);
+  else
+    k_decode16<__nv_bfloat16><<<1024, BLK, 0, s>>>(
+        g, Next, int_of_ext, static_cast<const __nv_bfloat16*>(pop), e, out, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_frozen(const Grid& g, int Next, const int* int_of_ext, int ncells,
-                          const int64_t* cells, const float* vals, void* pop, int storage,
-                          double* injection_acc, cudaStream_t s) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
+cudaError_t launch_frozen(const Grid& g, int Ni, int Next, const int* int_of_ext, int ncells,
+                          const int64_t* cells, const float* vals, void* pop, float* e,
+                          int storage, const DirTable& t, double* injection_acc, cudaStream_t s) {
   if (ncells <= 0) return cudaSuccess;
-  k_frozen<<<(ncells + BLK - 1) / BLK, BLK, 0, s>>>(g, Next, int_of_ext, ncells, cells, vals,
-                                                    static_cast<float*>(pop), injection_acc);
+  const int nb = (ncells + BLK - 1) / BLK;
+  if (storage == ST_F32)
+    k_frozen<<<nb, BLK, 0, s>>>(g, Next, int_of_ext, ncells, cells, vals,
+                                static_cast<float*>(pop), injection_acc);
+  else if (storage == ST_F16)
+    k_frozen16<__half><<<nb, BLK, 0, s>>>(g, Ni, Next, int_of_ext, ncells, cells, vals,
+                                          static_cast<__half*>(pop), e, injection_acc, t);
+  else
+    k_frozen16<__nv_bfloat16><<<nb, BLK, 0, s>>>(g, Ni, Next, int_of_ext, ncells, cells, vals,
+                                                 static_cast<__nv_bfloat16*>(pop), e,
+                                                 injection_acc, t);
   return cudaGetLastError();
 }
 
@@ -233,12 +448,19 @@ cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, int storage,
-                                double* partials, int max_blocks, double* out, cudaStream_t s) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
+cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, const float* e, int storage,
+                                const DirTable& t, double* partials, int max_blocks, double* out,
+                                cudaStream_t s) {
   int nb = (int)std::min<long long>((long long)max_blocks, (long long)grid1d(g.sites));
   if (nb < 1) nb = 1;
-  k_total_partials<<<nb, BLK, 0, s>>>(g, N, pop, partials);
+  if (storage == ST_F32)
+    k_total_partials<<<nb, BLK, 0, s>>>(g, N, pop, partials);
+  else if (storage == ST_F16)
+    k_total_partials16<__half><<<nb, BLK, 0, s>>>(g, N, static_cast<const __half*>(pop), e,
+                                                  partials, t);
+  else
+    k_total_partials16<__nv_bfloat16><<<nb, BLK, 0, s>>>(
+        g, N, static_cast<const __nv_bfloat16*>(pop), e, partials, t);
   k_sum_partials<<<1, BLK, 0, s>>>(partials, nb, out);
   return cudaGetLastError();
 }

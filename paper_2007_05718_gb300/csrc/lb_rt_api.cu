@@ -28,8 +28,10 @@ struct lb_rt {
   bool own_stream = false;
   int device = 0;
   void* pop[2] = {nullptr, nullptr};
-  float4* ef[2] = {nullptr, nullptr};  // per-site moments of the reduced-precision modes
+  float* ef[2] = {nullptr, nullptr};   // 16-bit storage: padded E arrays paired with pop[]
+  size_t ef_bytes = 0;
   CUtensorMap tmap[2];                 // TMA descriptors of pop[0] / pop[1]
+  CUtensorMap emap[2];                 // 16-bit storage: TMA descriptors of ef[0] / ef[1]
   bool tmap_ok = false;
   int cur = 0;
   size_t pop_bytes = 0;
@@ -150,24 +152,28 @@ void plan_directions(lb_rt* h) {
       });
     // the first plan (in the kernel's order of preference) that fits and
     // pads the direction set by at most 4 % more than the tightest plan
-    std::vector<int> ni_of(kNumTilePlans, -1);
+    const bool f32 = h->cfg.storage == LB_RT_F32;
+    const int (*plans)[3] = f32 ? kTilePlans : kTilePlans16;
+    const int nplans = f32 ? kNumTilePlans : kNumTilePlans16;
+    std::vector<int> ni_of(nplans, -1);
     int min_ni = 1 << 30;
-    for (int p = 0; p < kNumTilePlans; ++p) {
-      const int dpt = kTilePlans[p][0], zc = kTilePlans[p][1];
+    for (int p = 0; p < nplans; ++p) {
+      const int dpt = plans[p][0], zc = plans[p][1];
       if (zc > 1 && zc > h->grid.nz) continue;
       int ni = 0;
       for (auto& c : cls) ni += (int)(c.size() + dpt - 1) / dpt * dpt;
       const int warps = ni / dpt;
-      if (ni > kMaxInternalDirs || 32 * warps > kTilePlans[p][2]) continue;
-      if (step_tile_smem(dpt, zc, warps) > 227 * 1024) continue;
+      if (ni > kMaxInternalDirs || 32 * warps > plans[p][2]) continue;
+      const size_t smem = f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
+      if (smem > 227 * 1024) continue;
       ni_of[p] = ni;
       min_ni = std::min(min_ni, ni);
     }
     int best = -1;
-    for (int p = 0; p < kNumTilePlans && best < 0; ++p)
+    for (int p = 0; p < nplans && best < 0; ++p)
       if (ni_of[p] >= 0 && ni_of[p] * 100 <= min_ni * 104) best = p;
-    h->dpt = best >= 0 ? kTilePlans[best][0] : 0;
-    h->zc = best >= 0 ? kTilePlans[best][1] : 0;
+    h->dpt = best >= 0 ? plans[best][0] : 0;
+    h->zc = best >= 0 ? plans[best][1] : 0;
     for (auto& c : cls) {
       for (int e : c) h->ext_of_int.push_back(e);
       if (h->dpt)
@@ -223,8 +229,9 @@ lb_rt_status copy_in(lb_rt* h, void* dst, const void* src, size_t bytes, int ptr
 
 lb_rt_status reset_budget(lb_rt* h) {
   CK(h, cudaMemsetAsync(h->acc, 0, 8 * sizeof(double), h->stream));
-  cudaError_t e = launch_total_energy(h->grid, h->Ni, h->pop[h->cur], h->cfg.storage,
-                                      h->partials, h->partials_cap, h->acc, h->stream);
+  cudaError_t e = launch_total_energy(h->grid, h->Ni, h->pop[h->cur], h->ef[h->cur],
+                                      h->cfg.storage, h->table, h->partials, h->partials_cap,
+                                      h->acc, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "total energy");
   CK(h, cudaMemcpyAsync(h->acc + 1, h->acc, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   return LB_RT_OK;
@@ -265,7 +272,8 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   if (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
       cfg->storage != LB_RT_BF16_DEV)
     return bad("bad storage");
-  if (cfg->storage != LB_RT_F32) return bad("reduced-precision storage is not available yet");
+  if (cfg->storage != LB_RT_F32 && cfg->moving)
+    return bad("16-bit storage with a moving fluid is not available yet");
   if (cfg->collision != LB_RT_IMPLICIT_EXACT && cfg->collision != LB_RT_EXPLICIT &&
       cfg->collision != LB_RT_LAMBDA_K)
     return bad("bad collision");
@@ -324,8 +332,9 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   alloc(&h->pop[0], h->pop_bytes);
   alloc(&h->pop[1], h->pop_bytes);
   if (cfg->storage != LB_RT_F32) {
-    alloc((void**)&h->ef[0], sizeof(float4) * sites);
-    alloc((void**)&h->ef[1], sizeof(float4) * sites);
+    h->ef_bytes = sizeof(float) * (size_t)h->grid.PX * h->grid.PY * h->grid.PZ;
+    alloc((void**)&h->ef[0], h->ef_bytes);
+    alloc((void**)&h->ef[1], h->ef_bytes);
   }
   // budget partials: one slot pair per CTA of the step kernel; every step
   // kernel's grid is at most ceil(nx/32) x ny x nz CTAs
@@ -345,7 +354,8 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   // zero both buffers: ghost cells of vacuum faces stay zero for good
   e = cudaMemsetAsync(h->pop[0], 0, h->pop_bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, h->pop_bytes, h->stream);
-  if (e == cudaSuccess && h->ef[0]) e = cudaMemsetAsync(h->ef[0], 0, sizeof(float4) * sites, h->stream);
+  for (int b = 0; b < 2; ++b)
+    if (e == cudaSuccess && h->ef[b]) e = cudaMemsetAsync(h->ef[b], 0, h->ef_bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_int_of_ext, h->int_of_ext.data(), sizeof(int) * h->N,
@@ -357,17 +367,23 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     lb_rt_destroy(h);
     return LB_RT_ECUDA;
   }
-  if (cfg->storage == LB_RT_F32 && !cfg->moving) {
+  if (!cfg->moving) {
     std::string terr;
     for (int b = 0; b < 2; ++b) {
-      if (!make_pop_tensor_map(&h->tmap[b], h->grid, h->Ni, h->pop[b], h->dpt, h->zc, terr)) {
+      const bool ok =
+          cfg->storage == LB_RT_F32
+              ? make_pop_tensor_map(&h->tmap[b], h->grid, h->Ni, h->pop[b], h->dpt, h->zc, terr)
+              : make_pop16_tensor_map(&h->tmap[b], h->grid, h->Ni, h->pop[b], cfg->storage,
+                                      h->dpt, h->zc, terr) &&
+                    make_e_tensor_map(&h->emap[b], h->grid, h->ef[b], h->zc, terr);
+      if (!ok) {
         g_create_msg = terr;
         lb_rt_destroy(h);
         return LB_RT_ECUDA;
       }
     }
     h->tmap_ok = true;
-    e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, &h->nzc, &h->ctas);
+    e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, cfg->storage, &h->nzc, &h->ctas);
     if (e != cudaSuccess) {
       g_create_msg = std::string("static kernel grid: ") + cudaGetErrorString(e);
       lb_rt_destroy(h);
@@ -465,7 +481,7 @@ lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind
   }
   h->cur = 0;
   cudaError_t e = launch_init_state(h->grid, h->Ni, h->N, h->d_int_of_ext, src, kind, h->pop[0],
-                                    h->cfg.storage, h->table, h->stream);
+                                    h->ef[0], h->cfg.storage, h->table, h->stream);
   if (tmp) {
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
@@ -518,6 +534,8 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     L.in = h->pop[h->cur];
     L.out = h->pop[h->cur ^ 1];
     L.tmap_in = h->tmap_ok ? &h->tmap[h->cur] : nullptr;
+    L.tmap_e = h->ef[0] && h->tmap_ok ? &h->emap[h->cur] : nullptr;
+    L.e_out = h->ef[h->cur ^ 1];
     L.err = h->err;
     L.budget_partials = nullptr;
     L.partials_cap = h->partials_cap;
@@ -532,9 +550,9 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     ++launches;
     if (h->nfrozen) {
-      e = launch_frozen(h->grid, h->N, h->d_int_of_ext, h->nfrozen, h->frozen_cells,
-                        h->frozen_vals, h->pop[h->cur ^ 1], h->cfg.storage,
-                        h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
+      e = launch_frozen(h->grid, h->Ni, h->N, h->d_int_of_ext, h->nfrozen, h->frozen_cells,
+                        h->frozen_vals, h->pop[h->cur ^ 1], h->ef[h->cur ^ 1], h->cfg.storage,
+                        h->table, h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
     }
     if (h->cfg.budget) {
@@ -576,8 +594,8 @@ lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P, lb_rt_budget*
       dF = F ? h->scratch + S : nullptr;
       dP = P ? h->scratch + 4 * S : nullptr;
     }
-    cudaError_t e = launch_moments(h->grid, h->Ni, h->pop[h->cur], h->cfg.storage,
-                                   h->table, dE, dF, dP, h->stream);
+    cudaError_t e = launch_moments(h->grid, h->Ni, h->pop[h->cur], h->ef[h->cur],
+                                   h->cfg.storage, h->table, dE, dF, dP, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     if (ptr_kind == LB_RT_HOST) {
       if (E) CK(h, cudaMemcpyAsync(E, dE, sizeof(float) * S, cudaMemcpyDeviceToHost, h->stream));
@@ -612,7 +630,8 @@ lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
     return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   }
   cudaError_t e =
-      launch_decode(h->grid, h->N, h->d_int_of_ext, h->pop[h->cur], h->cfg.storage, dst, h->stream);
+      launch_decode(h->grid, h->N, h->d_int_of_ext, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
+                    h->table, dst, h->stream);
   if (e == cudaSuccess && tmp)
     e = cudaMemcpyAsync(out, tmp, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(h->stream);
@@ -624,7 +643,7 @@ lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
 size_t lb_rt_state_bytes(const lb_rt* h) {
   if (!h) return 0;
   size_t b = 64 + h->pop_bytes + 8 * sizeof(double);
-  if (h->ef[0]) b += sizeof(float4) * h->grid.sites;
+  if (h->ef[0]) b += h->ef_bytes;
   return b;
 }
 
@@ -638,9 +657,8 @@ lb_rt_status lb_rt_save_state(lb_rt* h, void* buf, size_t bytes) {
   CK(h, cudaMemcpyAsync(p, h->pop[h->cur], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream));
   p += h->pop_bytes;
   if (h->ef[0]) {
-    CK(h, cudaMemcpyAsync(p, h->ef[h->cur], sizeof(float4) * h->grid.sites, cudaMemcpyDeviceToHost,
-                          h->stream));
-    p += sizeof(float4) * h->grid.sites;
+    CK(h, cudaMemcpyAsync(p, h->ef[h->cur], h->ef_bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += h->ef_bytes;
   }
   CK(h, cudaMemcpyAsync(p, h->acc, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   return lb_rt_sync(h);
@@ -660,8 +678,8 @@ lb_rt_status lb_rt_restore_state(lb_rt* h, const void* buf, size_t bytes) {
   CK(h, cudaMemcpy(h->pop[h->cur], p, h->pop_bytes, cudaMemcpyHostToDevice));
   p += h->pop_bytes;
   if (h->ef[0]) {
-    CK(h, cudaMemcpy(h->ef[h->cur], p, sizeof(float4) * h->grid.sites, cudaMemcpyHostToDevice));
-    p += sizeof(float4) * h->grid.sites;
+    CK(h, cudaMemcpy(h->ef[h->cur], p, h->ef_bytes, cudaMemcpyHostToDevice));
+    p += h->ef_bytes;
   }
   CK(h, cudaMemcpy(h->acc, p, 8 * sizeof(double), cudaMemcpyHostToDevice));
   h->steps = hdr[4];

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <string>
@@ -85,6 +86,8 @@ struct StepLaunch {
   const void* in;      // populations at t (padded layout)
   void* out;           // populations at t + dt
   const CUtensorMap* tmap_in;  // TMA descriptor of `in` (host copy)
+  const CUtensorMap* tmap_e;   // 16-bit storage: TMA descriptor of the E array at t
+  float* e_out;                // 16-bit storage: E array at t + dt (padded, float32)
   double* budget_partials;  // [nblocks][2] (sum E*, sum E_collided) or nullptr
   long long partials_cap;   // slots available; a launcher whose grid is larger refuses
   unsigned* err;            // device error word
@@ -98,20 +101,23 @@ cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const D
                                int storage, cudaStream_t s, int* nblocks);
 // Ni = internal direction count; Next = external (user) count; int_of_ext =
 // device array mapping an external direction index to its internal one.
-cudaError_t launch_moments(const Grid& g, int Ni, const void* pop, int storage,
+// e = the padded float32 E array paired with `pop` (16-bit storage only).
+cudaError_t launch_moments(const Grid& g, int Ni, const void* pop, const float* e, int storage,
                            const DirTable& t, float* E, float* F, float* P, cudaStream_t s);
 cudaError_t launch_init_state(const Grid& g, int Ni, int Next, const int* int_of_ext,
-                              const float* data, int kind, void* pop, int storage,
+                              const float* data, int kind, void* pop, float* e, int storage,
                               const DirTable& t, cudaStream_t s);
 cudaError_t launch_decode(const Grid& g, int Next, const int* int_of_ext, const void* pop,
-                          int storage, float* out, cudaStream_t s);
-cudaError_t launch_frozen(const Grid& g, int Next, const int* int_of_ext, int ncells,
-                          const int64_t* cells, const float* vals, void* pop, int storage,
-                          double* injection_acc, cudaStream_t s);
+                          const float* e, int storage, const DirTable& t, float* out,
+                          cudaStream_t s);
+cudaError_t launch_frozen(const Grid& g, int Ni, int Next, const int* int_of_ext, int ncells,
+                          const int64_t* cells, const float* vals, void* pop, float* e,
+                          int storage, const DirTable& t, double* injection_acc, cudaStream_t s);
 cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* acc,
                                    cudaStream_t s);
-cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, int storage,
-                                double* partials, int max_blocks, double* out, cudaStream_t s);
+cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, const float* e, int storage,
+                                const DirTable& t, double* partials, int max_blocks, double* out,
+                                cudaStream_t s);
 
 // TMA descriptor of a padded float32 population buffer viewed as the 4D
 // tensor [PZ][PY][Ni][PX] with box (68, dpt, 2, zc) (kernels_tma.cu), and the
@@ -123,7 +129,20 @@ extern const int kNumTilePlans;
 size_t step_tile_smem(int dpt, int zc, int warps);
 // z chunks and CTA count of the static kernel's persistent grid for this
 // grid and plan on the current device (occupancy query).
-cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int* nzc, int* ctas);
+cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage, int* nzc,
+                             int* ctas);
+// 16-bit storage (kernels_tma16.cu): f_i = I_i / w_i = E (1 + q_i) with E a
+// padded float32 [PZ][PY][PX] array and q_i stored in FP16 or BF16.
+size_t step_tile_smem16(int dpt, int zc, int warps);
+extern const int kTilePlans16[][3];
+extern const int kNumTilePlans16;
+cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
+                                int storage, cudaStream_t s, int* nblocks);
+cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm);
+bool make_pop16_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int storage, int dpt,
+                           int zc, std::string& err);
+bool make_e_tensor_map(CUtensorMap* map, const Grid& g, float* base, int zc, std::string& err);
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(std::string& err);
 
 // Message returned by lb_rt_last_error(NULL) on this thread (calls without a handle).
 void set_unbound_error(const std::string& m);
