@@ -13,8 +13,9 @@ namespace tma {
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// a - b as one packed FMA, b (-1) + a (exact up to the single rounding)
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 // ---- mbarrier and TMA ------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -27,13 +28,16 @@ __device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
+// One bounded try: the thread may be suspended until the phase completes or
+// about 20 microseconds pass (the hint is in nanoseconds), so a waiting warp
+// does not take issue slots from the warps that have work.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
