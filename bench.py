@@ -50,21 +50,30 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic_from_profiles(kernel_tag):
-    """Per-launch DRAM bytes from the committed ncu summary, or None when the
-    kernel source changed after the capture."""
+PROFILE = os.path.join(ROOT, "profiles", "step_static_f32_sphere128_42.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2007_05718_gb300", "csrc", f)
+                  for f in ("kernels_tma.cu", "tma_common.cuh")]
+
+
+def kernel_source_hash():
     import hashlib
-    path = os.path.join(ROOT, "profiles", "step_static_f32_sphere128_42.md")
-    if not os.path.exists(path):
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profiles():
+    """Per-launch DRAM bytes of the step kernel from the committed ncu
+    summary, or None when the kernel source changed after the capture."""
+    if not os.path.exists(PROFILE):
         return None
-    src = open(os.path.join(ROOT, "paper_2007_05718_gb300", "csrc", "kernels_step.cu"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
     vals = {}
-    for line in open(path):
+    for line in open(PROFILE):
         if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16")):
             k, v = line.strip().split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != h:
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
@@ -265,6 +274,24 @@ def main():
         sd_step = sites * N
         value = sd_step * ws / (ms_max * 1e-3 / args.steps)
 
+        # the same workload with FP16 populations (16-bit deviation storage)
+        h16 = lbrt.lb_rt_create(3, N_SIDE, N_SIDE, N_SIDE, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL,
+                                cfl=CFL, dx=1.0 / N_SIDE, bc=(lbrt.LB_RT_VACUUM,) * 3,
+                                storage=lbrt.LB_RT_F16_DEV, stream=stream.cuda_stream)
+        lbrt.lb_rt_set_fluid(h16, kappa_a=ka, eta=eta)
+        lbrt.lb_rt_set_state(h16, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        lbrt.lb_rt_step(h16, args.warmup)
+        stream.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            lbrt.lb_rt_step(h16, 1)
+        f1.record(stream)
+        f1.synchronize()
+        ms16 = _max_over_ranks(ws, f0.elapsed_time(f1)) / args.steps
+        lbrt.lb_rt_destroy(h16)
+
         # end to end through the C ABI with host buffers
         ka_h = torch.from_numpy(sp["kappa_a"]).pin_memory()
         eta_h = torch.from_numpy(sp["eta"]).pin_memory()
@@ -299,7 +326,7 @@ def main():
     bytes_per_launch = sites * N * 8.0 + sites * 8.0   # populations r+w, kappa_a and eta fields
     peak, peak_kind = _peaks()
     achieved = bytes_per_launch / (ms_step * 1e-3) / 1e9
-    traffic = _traffic_from_profiles("step")
+    traffic = _traffic_from_profiles()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -314,6 +341,9 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * sites,
                 "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps},
         "clocks": ck,
+        "f16": {"value": sd_step * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
+                "ratio_vs_f32": ms_step / ms16,
+                "storage": "FP16 deviation from w_i E, float32 E per site, float32 arithmetic"},
     }
     if not args.no_cpu_baseline:
         try:
