@@ -51,17 +51,20 @@ struct DirConst {
   int sh, inert, pad0, pad1;
 };
 
-template <int DPT, int ZC, int R, int MAXT, int REGS>
+// BATCH = false: one problem, `one` and `tmap1` in the parameter space.
+// BATCH = true: `table[nprob]` in device memory; each CTA copies the
+// descriptor of its current tile into shared memory.
+template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
-k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const StaticCoef cf,
+k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
+           const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
            const DirTable t) {
   constexpr int SLOT = slot_floats<DPT, ZC>();
   static_assert(SLOT >= ZC * 4 * 64, "the partial moments must fit in a consumed slot");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
-  const Grid& gr = L.g;
-  const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+  __shared__ ProblemDesc pd[BATCH ? 2 : 1];
   // shared layout: ring [G][R][SLOT] | coef [ZC][5][64] | dirs [N] DirConst |
   // mbar [G][R] | budget [2 ZC][2] double | abort flag
   float* ring = reinterpret_cast<float*>(smem_raw);
@@ -71,10 +74,6 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   double* bsum = reinterpret_cast<double*>(mbar + G * R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 4 * ZC);
 
-  const int nxb = (nx + 63) / 64;
-  const int ntiles = nxb * ny * L.nzc;
-  const float inv_d = 1.f / (float)gr.dims;
-  float* __restrict__ out = static_cast<float*>(L.out);
   const int i0 = g * DPT;
   // the warp's row / plane class (uniform over its directions)
   const int oct0 = __float_as_int(t.au[i0].w);
@@ -113,10 +112,20 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   bool alive = true;
   int issued = 0, waited = 0;
   // issue cursor (tile, item), ahead of the consumer by up to R - 1 items
-  int is_t = blockIdx.x, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0;
+  int is_t = blockIdx.x, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0;
+  const CUtensorMap* is_map = &tmap1;
   auto issue_seek = [&]() {
     if (is_t < ntiles) {
-      const TileGeom tg = tile_geom(is_t, nxb, ny, nz, L.nzc);
+      if constexpr (BATCH) {
+        while (is_p < nprob && is_t >= table[is_p].tile_start + table[is_p].ntiles) ++is_p;
+        if (is_p >= nprob) {  // inconsistent table: stop issuing (the consumer reports it)
+          is_t = ntiles;
+          return;
+        }
+        is_map = table[is_p].tmap;
+      }
+      const ProblemDesc& D = BATCH ? table[is_p] : one;
+      const TileGeom tg = tile_geom(is_t - D.tile_start, (D.g.nx + 63) / 64, D.g.ny, D.g.nz, D.nzc);
       is_M = tile_items<ZC>(tg.zlen);
       is_x0 = tg.x0;
       is_yp = yneg ? tg.y + 1 : tg.y;  // lower padded row of the box
@@ -132,7 +141,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       const uint32_t bar = smem_u32(&mbar[g * R + slot]);
       fence_proxy_async();
       mbar_arrive_tx(bar, BOXX * DPT * 2 * ZC * 4);
-      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOT), &tmap, is_x0, i0, is_yp,
+      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOT), is_map, is_x0, i0, is_yp,
                   is_zp + is_m * ZC, bar);
     }
     ++issued;
@@ -148,7 +157,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
       alive = false;
       return false;
     }
-    if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), (uint32_t)((q / R) & 1), L.err)) {
+    if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), (uint32_t)((q / R) & 1), err)) {
       *abort_flag = 1;
       alive = false;
       return false;
@@ -166,9 +175,33 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   for (int k = 0; k < DPT; ++k) carry[k] = make_float2(0.f, 0.f);
   float bud_a = 0.f, bud_b = 0.f;  // FP32 per batch, folded into FP64 below
   double bud_da = 0.0, bud_db = 0.0;
-  int q = 0;  // items consumed
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const TileGeom tg = tile_geom(ti, nxb, ny, nz, L.nzc);
+  int q = 0;   // items consumed
+  int tk = 0;  // tiles taken by this CTA
+  int cp = 0;  // problem of the current tile
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++tk) {
+    const ProblemDesc* Pp = &one;
+    if constexpr (BATCH) {
+      while (cp < nprob && ti >= table[cp].tile_start + table[cp].ntiles) ++cp;
+      if (cp >= nprob) {  // the tile counts do not add up: report, stop (uniform per CTA)
+        if (g == 0 && lane == 0) atomicOr(err, 4u);
+        break;
+      }
+      ProblemDesc* dst = &pd[tk & 1];
+      if (g == 0) {
+        const int* src = reinterpret_cast<const int*>(&table[cp]);
+        for (int w = lane; w < (int)(sizeof(ProblemDesc) / 4); w += 32)
+          reinterpret_cast<int*>(dst)[w] = src[w];
+      }
+      __syncthreads();
+      Pp = dst;
+    }
+    const ProblemDesc& P = *Pp;
+    const Grid& gr = P.g;
+    const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+    const float inv_d = 1.f / (float)gr.dims;
+    float* __restrict__ out = static_cast<float*>(P.out);
+    const StaticCoef& cf = P.cf;
+    const TileGeom tg = tile_geom(ti - P.tile_start, (nx + 63) / 64, ny, nz, P.nzc);
     const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
     const int M = tile_items<ZC>(tg.zlen);
     const int xa = x0 + 2 * lane;  // the lane's pair (xa, xa + 1)
@@ -272,7 +305,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
           Fz += p[192];
         }
         const Coef cc =
-            collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, ka, k0, lam, eta, E, Fx, Fy, Fz);
+            collide_scalars(P.collision, P.lambda_iters, P.dt, inv_d, ka, k0, lam, eta, E, Fx, Fy, Fz);
         float* c = coef + j * 5 * 64 + f;
         c[0] = cc.alpha;
         c[64] = cc.c0;
@@ -285,7 +318,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
         }
       }
       __syncthreads();
-      if (L.budget_partials && g < nunits) {
+      if (!BATCH && one.budget_partials && g < nunits) {
         bud_da += (double)bud_a;
         bud_db += (double)bud_b;
         bud_a = bud_b = 0.f;
@@ -378,9 +411,9 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
   // copies still in flight (only after a failed wait) must land before the
   // CTA's shared memory is released; each slot has at most one outstanding
   for (int qq = waited; qq < issued; ++qq) {
-    mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), L.err);
+    mbar_wait(smem_u32(&mbar[g * R + qq % R]), (uint32_t)((qq / R) & 1), err);
   }
-  if (L.budget_partials) {
+  if (!BATCH && one.budget_partials) {
     for (int s = 16; s > 0; s >>= 1) {
       bud_da += __shfl_xor_sync(0xffffffffu, bud_da, s);
       bud_db += __shfl_xor_sync(0xffffffffu, bud_db, s);
@@ -396,8 +429,8 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap, const StepLaunch L, const S
         a += bsum[2 * w];
         b += bsum[2 * w + 1];
       }
-      atomicAdd(L.budget_partials + 2 * blockIdx.x, a);
-      atomicAdd(L.budget_partials + 2 * blockIdx.x + 1, b);
+      atomicAdd(one.budget_partials + 2 * blockIdx.x, a);
+      atomicAdd(one.budget_partials + 2 * blockIdx.x + 1, b);
     }
   }
 }
@@ -408,26 +441,26 @@ size_t step_smem(int G) {
          sizeof(DirConst) * (size_t)G * DPT + 8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
 }
 
-template <int DPT, int ZC, int R, int MAXT, int REGS>
+template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr() {
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<DPT, ZC, R, MAXT, REGS>,
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<BATCH, DPT, ZC, R, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+                                             227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
   return e;
 }
 
-template <int DPT, int ZC, int R, int MAXT, int REGS>
+template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy(int G, int* per_sm) {
-  cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, REGS>();
+  cudaError_t e = set_smem_attr<BATCH, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_step_f32<DPT, ZC, R, MAXT, REGS>,
-                                                       32 * G, step_smem<DPT, ZC, R>(G));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      per_sm, k_step_f32<BATCH, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
 }
 
 template <int DPT, int ZC, int R, int MAXT, int REGS>
@@ -440,10 +473,41 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   if (L.budget_partials && L.ctas > L.partials_cap) return cudaErrorInvalidValue;
   if (nblocks) *nblocks = L.ctas;
   const size_t smem = step_smem<DPT, ZC, R>(G);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr<DPT, ZC, R, MAXT, REGS>();
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t e = set_smem_attr<false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
-  k_step_f32<DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, L, c, t);
+  ProblemDesc one{};
+  one.g = L.g;
+  one.out = L.out;
+  one.tmap = nullptr;
+  one.cf = c;
+  one.dt = L.dt;
+  one.collision = L.collision;
+  one.lambda_iters = L.lambda_iters;
+  one.nzc = L.nzc;
+  one.tile_start = 0;
+  one.ntiles = (L.g.nx + 63) / 64 * L.g.ny * L.nzc;
+  one.budget_partials = L.budget_partials;
+  k_step_f32<false, DPT, ZC, R, MAXT, REGS>
+      <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
+  return cudaGetLastError();
+}
+
+template <int DPT, int ZC, int R, int MAXT, int REGS>
+cudaError_t launch_f32_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+  const int G = B.N / DPT;
+  if (G < 1 || G * DPT != B.N || 32 * G > MAXT || B.ctas < 1 || B.ntiles < 1 || !B.table ||
+      B.nprob < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = step_smem<DPT, ZC, R>(G);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t e = set_smem_attr<true, DPT, ZC, R, MAXT, REGS>();
+  if (e != cudaSuccess) return e;
+  // the parameter-space tensor map and descriptor are unused by the batched kernel
+  CUtensorMap unused{};
+  ProblemDesc none{};
+  k_step_f32<true, DPT, ZC, R, MAXT, REGS>
+      <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   return cudaGetLastError();
 }
 
@@ -478,6 +542,25 @@ size_t step_tile_smem(int dpt, int zc, int warps) {
   return (size_t)-1;
 }
 
+cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+  if (B.storage != ST_F32) return launch_tma16_static_batch(B, t, s);
+#define LBRT_LAUNCHB(D, Z, T, R_) \
+  if (B.dpt == D && B.zc == Z) return launch_f32_batch<D, Z, kRing, T, R_>(B, t, s);
+  LBRT_TILE_PLANS(LBRT_LAUNCHB)
+#undef LBRT_LAUNCHB
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm) {
+  if (storage != ST_F32) return occupancy_tma16(storage, dpt, zc, G, per_sm, true);
+  cudaError_t e = cudaErrorInvalidValue;
+#define LBRT_OCCB(D, Z, T, R_) \
+  if (dpt == D && zc == Z) e = occupancy<true, D, Z, kRing, T, R_>(G, per_sm);
+  LBRT_TILE_PLANS(LBRT_OCCB)
+#undef LBRT_OCCB
+  return e;
+}
+
 cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                               int dpt, int zc, cudaStream_t s, int* nblocks) {
 #define LBRT_LAUNCH(D, Z, T, B) \
@@ -499,7 +582,7 @@ cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage
   cudaError_t e = cudaErrorInvalidValue;
   if (storage == ST_F32) {
 #define LBRT_OCC(D, Z, T, B) \
-  if (dpt == D && zc == Z) e = occupancy<D, Z, kRing, T, B>(G, &per_sm);
+  if (dpt == D && zc == Z) e = occupancy<false, D, Z, kRing, T, B>(G, &per_sm);
     LBRT_TILE_PLANS(LBRT_OCC)
 #undef LBRT_OCC
   } else {

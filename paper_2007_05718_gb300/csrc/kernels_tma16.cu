@@ -82,10 +82,13 @@ __device__ __forceinline__ void store_e(float* e, const Grid& g, int z, int y, i
       for (int c = 0; c < nxs; ++c) e[zs[a] * ez + ys[b] * ey + xs[c]] = v;
 }
 
-template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
+// BATCH as in the float32 kernel: one problem in the parameter space, or a
+// device array of problem descriptors walked by the persistent CTAs.
+template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
-k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap emap,
-          const StepLaunch L, const StaticCoef cf, const DirTable t) {
+k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUtensorMap emap1,
+          const __grid_constant__ ProblemDesc one, const ProblemDesc* __restrict__ table,
+          int nprob, int ntiles, unsigned* err, const DirTable t) {
   using C2 = Conv<ST>;
   using T2 = typename C2::T2;
   constexpr int SLOTB = slot_bytes16<DPT, ZC>();
@@ -94,8 +97,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
-  const Grid& gr = L.g;
-  const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+  __shared__ ProblemDesc pd[BATCH ? 2 : 1];
   // shared layout: ring [G][R][SLOTB] | E ring [R][ESLOT] | coef [ZC][5][64] |
   // dirs [N] | mbar [G][R] | ebar [R] | budget [2 ZC][2] double | abort flag
   unsigned char* ring = smem_raw;
@@ -107,11 +109,6 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
   double* bsum = reinterpret_cast<double*>(ebar + R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 4 * ZC);
 
-  const int nxb = (nx + 63) / 64;
-  const int ntiles = nxb * ny * L.nzc;
-  const float inv_d = 1.f / (float)gr.dims;
-  ST* __restrict__ out = static_cast<ST*>(L.out);
-  float* __restrict__ eout = L.e_out;
   const int i0 = g * DPT;
   const int oct0 = __float_as_int(t.au[i0].w);
   const bool yneg = oct0 & 2;
@@ -151,10 +148,23 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
   unsigned char* my_ring = ring + (size_t)g * R * SLOTB;
   bool alive = true;
   int issued = 0, waited = 0;
-  int is_t = blockIdx.x, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0, is_y = 0, is_zb = 0;
+  int is_t = blockIdx.x, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0, is_y = 0,
+      is_zb = 0;
+  const CUtensorMap* is_map = &tmap1;
+  const CUtensorMap* is_emap = &emap1;
   auto issue_seek = [&]() {
     if (is_t < ntiles) {
-      const TileGeom tg = tile_geom(is_t, nxb, ny, nz, L.nzc);
+      if constexpr (BATCH) {
+        while (is_p < nprob && is_t >= table[is_p].tile_start + table[is_p].ntiles) ++is_p;
+        if (is_p >= nprob) {  // inconsistent table: stop issuing (the consumer reports it)
+          is_t = ntiles;
+          return;
+        }
+        is_map = table[is_p].tmap;
+        is_emap = table[is_p].emap;
+      }
+      const ProblemDesc& D = BATCH ? table[is_p] : one;
+      const TileGeom tg = tile_geom(is_t - D.tile_start, (D.g.nx + 63) / 64, D.g.ny, D.g.nz, D.nzc);
       is_M = tile_items<ZC>(tg.zlen);
       is_x0 = tg.x0;
       is_y = tg.y;
@@ -172,12 +182,12 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
       const uint32_t bar = smem_u32(&mbar[g * R + slot]);
       fence_proxy_async();
       mbar_arrive_tx(bar, BOXH * DPT * 2 * ZC * 2);
-      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOTB), &tmap, is_x0, i0, is_yp,
+      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOTB), is_map, is_x0, i0, is_yp,
                   is_zp + is_m * ZC, bar);
       if (g == 0) {
         const uint32_t eb = smem_u32(&ebar[slot]);
         mbar_arrive_tx(eb, BOXH * 3 * (ZC + 1) * 4);
-        tma_load_3d(smem_u32(ering + (size_t)slot * ESLOT), &emap, is_x0, is_y,
+        tma_load_3d(smem_u32(ering + (size_t)slot * ESLOT), is_emap, is_x0, is_y,
                     is_zb + is_m * ZC, eb);
       }
     }
@@ -195,8 +205,8 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
       return false;
     }
     const uint32_t par = (uint32_t)((q / R) & 1);
-    if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), par, L.err) ||
-        !mbar_wait(smem_u32(&ebar[q % R]), par, L.err)) {
+    if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), par, err) ||
+        !mbar_wait(smem_u32(&ebar[q % R]), par, err)) {
       *abort_flag = 1;
       alive = false;
       return false;
@@ -215,8 +225,33 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
   float bud_a = 0.f, bud_b = 0.f;
   double bud_da = 0.0, bud_db = 0.0;
   int q = 0;
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const TileGeom tg = tile_geom(ti, nxb, ny, nz, L.nzc);
+  int tk = 0;
+  int cp = 0;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++tk) {
+    const ProblemDesc* Pp = &one;
+    if constexpr (BATCH) {
+      while (cp < nprob && ti >= table[cp].tile_start + table[cp].ntiles) ++cp;
+      if (cp >= nprob) {  // the tile counts do not add up: report, stop (uniform per CTA)
+        if (g == 0 && lane == 0) atomicOr(err, 4u);
+        break;
+      }
+      ProblemDesc* dst = &pd[tk & 1];
+      if (g == 0) {
+        const int* src = reinterpret_cast<const int*>(&table[cp]);
+        for (int w = lane; w < (int)(sizeof(ProblemDesc) / 4); w += 32)
+          reinterpret_cast<int*>(dst)[w] = src[w];
+      }
+      __syncthreads();
+      Pp = dst;
+    }
+    const ProblemDesc& P = *Pp;
+    const Grid& gr = P.g;
+    const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+    const float inv_d = 1.f / (float)gr.dims;
+    ST* __restrict__ out = static_cast<ST*>(P.out);
+    float* __restrict__ eout = P.e_out;
+    const StaticCoef& cf = P.cf;
+    const TileGeom tg = tile_geom(ti - P.tile_start, (nx + 63) / 64, ny, nz, P.nzc);
     const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
     const int M = tile_items<ZC>(tg.zlen);
     const int xa = x0 + 2 * lane;
@@ -342,7 +377,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
           Fz += p[192];
         }
         const Coef cc =
-            collide_scalars(L.collision, L.lambda_iters, L.dt, inv_d, ka, k0, lam, eta, E, Fx, Fy, Fz);
+            collide_scalars(P.collision, P.lambda_iters, P.dt, inv_d, ka, k0, lam, eta, E, Fx, Fy, Fz);
         // q' = f' / E^' - 1 with E^' = max(E', eps): the coefficients of the
         // float32 path scaled by 1 / E^'
         const float Eh = fmaxf(cc.Enew, EPS_E);
@@ -360,7 +395,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
         }
       }
       __syncthreads();
-      if (L.budget_partials && g < nunits) {
+      if (!BATCH && one.budget_partials && g < nunits) {
         bud_da += (double)bud_a;
         bud_db += (double)bud_b;
         bud_a = bud_b = 0.f;
@@ -439,10 +474,10 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
   }
   for (int qq = waited; qq < issued; ++qq) {
     const uint32_t par = (uint32_t)((qq / R) & 1);
-    mbar_wait(smem_u32(&mbar[g * R + qq % R]), par, L.err);
-    if (g == 0) mbar_wait(smem_u32(&ebar[qq % R]), par, L.err);
+    mbar_wait(smem_u32(&mbar[g * R + qq % R]), par, err);
+    if (g == 0) mbar_wait(smem_u32(&ebar[qq % R]), par, err);
   }
-  if (L.budget_partials) {
+  if (!BATCH && one.budget_partials) {
     for (int s = 16; s > 0; s >>= 1) {
       bud_da += __shfl_xor_sync(0xffffffffu, bud_da, s);
       bud_db += __shfl_xor_sync(0xffffffffu, bud_db, s);
@@ -458,8 +493,8 @@ k_step_16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
         a += bsum[2 * w];
         b += bsum[2 * w + 1];
       }
-      atomicAdd(L.budget_partials + 2 * blockIdx.x, a);
-      atomicAdd(L.budget_partials + 2 * blockIdx.x + 1, b);
+      atomicAdd(one.budget_partials + 2 * blockIdx.x, a);
+      atomicAdd(one.budget_partials + 2 * blockIdx.x + 1, b);
     }
   }
 }
@@ -470,24 +505,25 @@ size_t step_smem16(int G) {
          sizeof(DirConst16) * (size_t)G * DPT + 8 * ((size_t)G * R + R) + sizeof(double) * 4 * ZC + 16;
 }
 
-template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
+template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr16() {
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_16<ST, DPT, ZC, R, MAXT, REGS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const cudaError_t e = cudaFuncSetAttribute(k_step_16<ST, BATCH, DPT, ZC, R, MAXT, REGS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
   return e;
 }
 
-template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
+template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy16(int G, int* per_sm) {
-  cudaError_t e = set_smem_attr16<ST, DPT, ZC, R, MAXT, REGS>();
+  cudaError_t e = set_smem_attr16<ST, BATCH, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      per_sm, k_step_16<ST, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem16<DPT, ZC, R>(G));
+      per_sm, k_step_16<ST, BATCH, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem16<DPT, ZC, R>(G));
 }
 
 template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
@@ -500,10 +536,40 @@ cudaError_t launch16(const StepLaunch& L, const StaticCoef& c, const DirTable& t
   if (L.budget_partials && L.ctas > L.partials_cap) return cudaErrorInvalidValue;
   if (nblocks) *nblocks = L.ctas;
   const size_t smem = step_smem16<DPT, ZC, R>(G);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr16<ST, DPT, ZC, R, MAXT, REGS>();
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t e = set_smem_attr16<ST, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
-  k_step_16<ST, DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, *L.tmap_e, L, c, t);
+  ProblemDesc one{};
+  one.g = L.g;
+  one.out = L.out;
+  one.e_out = L.e_out;
+  one.cf = c;
+  one.dt = L.dt;
+  one.collision = L.collision;
+  one.lambda_iters = L.lambda_iters;
+  one.nzc = L.nzc;
+  one.tile_start = 0;
+  one.ntiles = (L.g.nx + 63) / 64 * L.g.ny * L.nzc;
+  one.budget_partials = L.budget_partials;
+  k_step_16<ST, false, DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(
+      *L.tmap_in, *L.tmap_e, one, nullptr, 1, one.ntiles, L.err, t);
+  return cudaGetLastError();
+}
+
+template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
+cudaError_t launch16_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+  const int G = B.N / DPT;
+  if (G < 1 || G * DPT != B.N || 32 * G > MAXT || B.ctas < 1 || B.ntiles < 1 || !B.table ||
+      B.nprob < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = step_smem16<DPT, ZC, R>(G);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t e = set_smem_attr16<ST, true, DPT, ZC, R, MAXT, REGS>();
+  if (e != cudaSuccess) return e;
+  CUtensorMap unused{};
+  ProblemDesc none{};
+  k_step_16<ST, true, DPT, ZC, R, MAXT, REGS><<<B.ctas, dim3(32, G), smem, s>>>(
+      unused, unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   return cudaGetLastError();
 }
 
@@ -531,11 +597,22 @@ cudaError_t launch_typed(const StepLaunch& L, const StaticCoef& c, const DirTabl
 }
 
 template <class ST>
-cudaError_t occupancy_typed(int dpt, int zc, int G, int* per_sm) {
+cudaError_t occupancy_typed(int dpt, int zc, int G, int* per_sm, bool batch) {
 #define LBRT_O16(D, Z, T, B) \
-  if (dpt == D && zc == Z) return occupancy16<ST, D, Z, kRing16, T, B>(G, per_sm);
+  if (dpt == D && zc == Z)                                                              \
+    return batch ? occupancy16<ST, true, D, Z, kRing16, T, B>(G, per_sm)                \
+                 : occupancy16<ST, false, D, Z, kRing16, T, B>(G, per_sm);
   LBRT_TILE_PLANS16(LBRT_O16)
 #undef LBRT_O16
+  return cudaErrorInvalidValue;
+}
+
+template <class ST>
+cudaError_t launch_typed_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+#define LBRT_LB16(D, Z, T, R_) \
+  if (B.dpt == D && B.zc == Z) return launch16_batch<ST, D, Z, kRing16, T, R_>(B, t, s);
+  LBRT_TILE_PLANS16(LBRT_LB16)
+#undef LBRT_LB16
   return cudaErrorInvalidValue;
 }
 
@@ -561,9 +638,15 @@ cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm) {
-  if (storage == ST_F16) return occupancy_typed<__half>(dpt, zc, G, per_sm);
-  if (storage == ST_BF16) return occupancy_typed<__nv_bfloat16>(dpt, zc, G, per_sm);
+cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch) {
+  if (storage == ST_F16) return occupancy_typed<__half>(dpt, zc, G, per_sm, batch);
+  if (storage == ST_BF16) return occupancy_typed<__nv_bfloat16>(dpt, zc, G, per_sm, batch);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tma16_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+  if (B.storage == ST_F16) return launch_typed_batch<__half>(B, t, s);
+  if (B.storage == ST_BF16) return launch_typed_batch<__nv_bfloat16>(B, t, s);
   return cudaErrorInvalidValue;
 }
 

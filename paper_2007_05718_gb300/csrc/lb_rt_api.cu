@@ -165,7 +165,7 @@ void plan_directions(lb_rt* h) {
       const int warps = ni / dpt;
       if (ni > kMaxInternalDirs || 32 * warps > plans[p][2]) continue;
       const size_t smem = f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
-      if (smem > 227 * 1024) continue;
+      if (smem > 226 * 1024) continue;
       ni_of[p] = ni;
       min_ni = std::min(min_ni, ni);
     }

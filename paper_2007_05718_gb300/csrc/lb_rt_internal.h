@@ -93,6 +93,38 @@ struct StepLaunch {
   unsigned* err;            // device error word
 };
 
+// One problem of a static step launch.  The single-problem launch passes it
+// as a kernel parameter; the batched launch passes a device array of them
+// (with the tensor maps in device memory) and the persistent CTAs walk the
+// concatenation of all problems' tiles, tiles [tile_start, tile_start +
+// ntiles) belonging to this problem.
+struct ProblemDesc {
+  Grid g;
+  void* out;                  // populations at t + dt (padded layout)
+  float* e_out;               // 16-bit storage: E array at t + dt
+  const CUtensorMap* tmap;    // TMA descriptor of the populations at t (batched launch)
+  const CUtensorMap* emap;    // 16-bit storage: TMA descriptor of the E array at t
+  StaticCoef cf;
+  float dt;
+  int collision, lambda_iters;
+  int nzc;                    // z chunks per column of tiles
+  int tile_start, ntiles;
+  double* budget_partials;    // single-problem launch only
+};
+
+// A batched static step: every problem of `table` (device memory) has the
+// same internal direction table, plan and storage.
+struct BatchLaunch {
+  const ProblemDesc* table;  // device array
+  int nprob, ntiles;         // problems, total tiles
+  int N, dpt, zc, storage;
+  int ctas;
+  unsigned* err;
+};
+cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
+cudaError_t launch_tma16_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
+cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm);
+
 // Kernel launchers.  Return cudaGetLastError() (or an error without
 // launching when the configuration is not supported).
 cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
@@ -138,7 +170,7 @@ extern const int kTilePlans16[][3];
 extern const int kNumTilePlans16;
 cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                                 int storage, cudaStream_t s, int* nblocks);
-cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm);
+cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch = false);
 bool make_pop16_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int storage, int dpt,
                            int zc, std::string& err);
 bool make_e_tensor_map(CUtensorMap* map, const Grid& g, float* base, int zc, std::string& err);
