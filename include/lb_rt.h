@@ -46,7 +46,8 @@ typedef enum {
   LB_RT_ENOMEM = -2,    /* device or host allocation failed */
   LB_RT_ECUDA = -3,     /* a CUDA runtime call failed */
   LB_RT_ETIMEDOUT = -4, /* a bounded device wait gave up */
-  LB_RT_ESTATE = -5     /* call not valid in the handle's current state */
+  LB_RT_ESTATE = -5,    /* call not valid in the handle's current state */
+  LB_RT_EBUSY = -6      /* batch: the problem does not fit the free memory or slots now */
 } lb_rt_status;
 
 /* built-in direction sets (used when lb_rt_config.dirs == NULL) */
@@ -188,6 +189,84 @@ lb_rt_status lb_rt_directions(const lb_rt* h, int* ndir, double* dirs, double* w
  * -- valid after lb_rt_sync(). Returns EINVAL if timing was not enabled. */
 lb_rt_status lb_rt_enable_timing(lb_rt* h, int on);
 lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch);
+
+/* ---- Batched problems (many independent solves in one launch) ----------
+ *
+ * Not a construct of the paper, which solves one problem at a time: a batch
+ * keeps many independent static-fluid problems resident on the device and
+ * advances them together.  Problems whose direction table, tile plan and
+ * storage agree form one group; each step of a group is ONE persistent
+ * kernel launch over the concatenated tiles of all its problems (Sec. 3.3
+ * stream and collision per problem, exactly as lb_rt_step), and a tick (the
+ * steps_per_tick steps of every group) is captured into a CUDA graph and
+ * replayed while its launch plan is unchanged.  An autotuner picks, per
+ * group, the z-chunk length of the tiles by timing the candidates on the
+ * first ticks of a new set of problems.  Admission is by device memory: a
+ * problem is admitted when its buffers fit the batch's budget and a slot is
+ * free; otherwise lb_rt_batch_admit returns LB_RT_EBUSY and the caller
+ * retries after completed problems are released.  Batched problems have no
+ * energy budget, no frozen cells and a static fluid.  The result of a
+ * problem is the same alone and in any mix: its tiles depend only on its
+ * own data. */
+typedef struct lb_rt_batch lb_rt_batch;
+
+#define LB_RT_BATCH_MAX 256
+
+typedef struct {
+  size_t mem_budget;   /* device bytes for admitted problems; 0 => 80 % of free memory at create */
+  int max_problems;    /* slots, 1 .. LB_RT_BATCH_MAX */
+  int storage;         /* LB_RT_F32 | LB_RT_F16_DEV | LB_RT_BF16_DEV, every problem */
+  int steps_per_tick;  /* steps per lb_rt_batch_tick, >= 1 */
+  int use_graph;       /* 1: capture ticks into a CUDA graph */
+  int autotune;        /* 1: time the tile z-chunk candidates on new sets of problems */
+  void* stream;        /* cudaStream_t; NULL => the batch creates one */
+} lb_rt_batch_config;
+
+lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out);
+void lb_rt_batch_destroy(lb_rt_batch* b);
+
+/* Device bytes a problem with this configuration would hold (populations,
+ * moment field, coefficient fields, staging); 0 with an invalid cfg. */
+size_t lb_rt_batch_problem_bytes(const lb_rt_batch* b, const lb_rt_config* cfg);
+
+/* Admit a problem: cfg as for lb_rt_create (storage and stream are taken
+ * from the batch; moving and budget must be 0), its fluid fields and
+ * initial state as for lb_rt_set_fluid / lb_rt_set_state, and the number of
+ * steps to run.  *slot receives its slot.  Errors: EINVAL, EBUSY (does not
+ * fit now), ENOMEM, ECUDA. */
+lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb_rt_fluid* fluid,
+                               int fluid_ptr_kind, const float* state, int state_kind,
+                               int state_ptr_kind, long long nsteps, int* slot);
+
+/* Enqueue one tick: every active problem advances by min(steps_per_tick,
+ * remaining steps).  *n_active (may be NULL) receives the number of
+ * problems that took part.  Asynchronous on the batch stream (the call
+ * first waits for the previous tick, whose tables it reuses). */
+lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active);
+
+/* Wait for the enqueued ticks and surface device errors. */
+lb_rt_status lb_rt_batch_sync(lb_rt_batch* b);
+
+/* Slots whose problems have run all their steps and are not yet released
+ * (call after lb_rt_batch_sync).  Writes at most max slots; *n the count. */
+lb_rt_status lb_rt_batch_poll(lb_rt_batch* b, int* slots, int max, int* n);
+
+/* Moments of a problem's current state, as lb_rt_moments (budget NULL). */
+lb_rt_status lb_rt_batch_moments(lb_rt_batch* b, int slot, float* E, float* F, float* P,
+                                 int ptr_kind);
+
+/* Steps done by the problem in `slot`. */
+lb_rt_status lb_rt_batch_steps(const lb_rt_batch* b, int slot, long long* steps);
+
+/* Free a problem's device memory and its slot. */
+lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot);
+
+/* The autotuner's current choice for the group of `slot`: z-chunk length
+ * (planes per tile) and CTAs of its last persistent launch. */
+lb_rt_status lb_rt_batch_tuning(const lb_rt_batch* b, int slot, int* zchunk, int* ctas);
+
+/* Message of the batch's last error. */
+const char* lb_rt_batch_last_error(const lb_rt_batch* b);
 
 /* FP64 total energy sum_sites sum_i I_i of a dense float32 population array
  * pop [ndir][sites] in device memory (for example the output of

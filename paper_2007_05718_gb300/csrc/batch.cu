@@ -1,0 +1,498 @@
+// Batch runtime of the C ABI (lb_rt_batch_* in include/lb_rt.h): many
+// independent static-fluid problems resident on one device, admitted by
+// device memory, grouped by direction table and advanced together with one
+// persistent kernel launch per group and step (the batched form of the
+// TMA-fed step kernels), a CUDA graph per launch plan and a z-chunk
+// autotuner.  The paper solves one problem at a time; this layer is the
+// library's own.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+#include "lb_rt_internal.h"
+
+using namespace lbrt;
+
+namespace {
+
+struct Member {
+  lb_rt* h = nullptr;
+  long long nsteps = 0;
+  size_t bytes = 0;
+  int group = -1;
+  bool used = false;
+};
+
+// Problems that share the internal direction table, tile plan and storage.
+struct Group {
+  DirTable table{};
+  int Ni = 0, dpt = 0, zc = 0;
+  int per_sm = 0;         // resident CTAs per SM of the batched kernel
+  int zchunk = 16;        // planes per tile
+  // autotuner: candidates are timed on successive ticks of a new member set
+  std::vector<int> cands;
+  std::vector<double> cost;  // ms per (site x step) of each candidate
+  int cand = 0;
+  bool tuned = false;
+  long long tuned_sites = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int ctas = 0;           // CTAs of the last launch
+};
+
+constexpr int kZCandidates[] = {8, 16, 32, 64};
+
+}  // namespace
+
+struct lb_rt_batch {
+  lb_rt_batch_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0, used = 0;
+  int sms = 0;
+  std::vector<Member> slots;
+  std::vector<Group> groups;
+  // descriptor tables: host staging (pinned) and device copy
+  ProblemDesc* h_desc = nullptr;
+  ProblemDesc* d_desc = nullptr;
+  size_t desc_cap = 0;
+  // tensor maps of every slot: [slot][parity][pop, E]
+  CUtensorMap* h_maps = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  bool maps_dirty = true;
+  unsigned* d_err = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the launch plan the graph was captured for: per launch (group, first
+  // descriptor, problems, tiles) and per descriptor (slot, z chunks); a
+  // graph is replayed only for an identical plan
+  std::vector<long long> graph_sig;
+  std::string msg;
+};
+
+namespace {
+
+lb_rt_status bfail(lb_rt_batch* b, lb_rt_status st, const std::string& m) {
+  if (b) b->msg = m;
+  return st;
+}
+
+lb_rt_status bcuda(lb_rt_batch* b, cudaError_t e, const char* where) {
+  return bfail(b, e == cudaErrorMemoryAllocation ? LB_RT_ENOMEM : LB_RT_ECUDA,
+               std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BCK(b, call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call); \
+  } while (0)
+
+bool same_table(const Group& g, const lb_rt* h) {
+  return g.Ni == h->Ni && g.dpt == h->dpt && g.zc == h->zc &&
+         std::memcmp(&g.table, &h->table, sizeof(DirTable)) == 0;
+}
+
+struct Launch {
+  int group, first, nprob, ntiles;
+};
+
+}  // namespace
+
+extern "C" {
+
+lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out) {
+  if (!cfg || !out) return LB_RT_EINVAL;
+  *out = nullptr;
+  if (cfg->max_problems < 1 || cfg->max_problems > LB_RT_BATCH_MAX || cfg->steps_per_tick < 1 ||
+      (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
+       cfg->storage != LB_RT_BF16_DEV))
+    return LB_RT_EINVAL;
+  lb_rt_batch* b = new (std::nothrow) lb_rt_batch();
+  if (!b) return LB_RT_ENOMEM;
+  b->cfg = *cfg;
+  b->slots.resize(cfg->max_problems);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    if (cfg->stream) {
+      b->stream = (cudaStream_t)cfg->stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      b->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e == cudaSuccess) {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    b->budget = cfg->mem_budget ? cfg->mem_budget : (size_t)(0.8 * (double)fr);
+  }
+  const size_t nmaps = (size_t)cfg->max_problems * 4;
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_maps, sizeof(CUtensorMap) * nmaps);
+  if (e == cudaSuccess) std::memset(b->h_maps, 0, sizeof(CUtensorMap) * nmaps);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_maps, sizeof(CUtensorMap) * nmaps);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    lb_rt_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? LB_RT_ENOMEM : LB_RT_ECUDA;
+  }
+  *out = b;
+  return LB_RT_OK;
+}
+
+void lb_rt_batch_destroy(lb_rt_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& m : b->slots)
+    if (m.h) lb_rt_destroy(m.h);
+  for (auto& g : b->groups) {
+    if (g.ev0) cudaEventDestroy(g.ev0);
+    if (g.ev1) cudaEventDestroy(g.ev1);
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFreeHost(b->h_desc);
+  cudaFree(b->d_desc);
+  cudaFreeHost(b->h_maps);
+  cudaFree(b->d_maps);
+  cudaFree(b->d_err);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+size_t lb_rt_batch_problem_bytes(const lb_rt_batch* b, const lb_rt_config* cfg) {
+  if (!b || !cfg) return 0;
+  lb_rt_config c = *cfg;
+  c.storage = b->cfg.storage;
+  std::string err;
+  return handle_device_bytes(c, err);
+}
+
+lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb_rt_fluid* fluid,
+                               int fluid_ptr_kind, const float* state, int state_kind,
+                               int state_ptr_kind, long long nsteps, int* slot) {
+  if (!b) return LB_RT_EINVAL;
+  if (!cfg || !fluid || !state || !slot || nsteps < 0)
+    return bfail(b, LB_RT_EINVAL, "null argument or negative step count");
+  if (cfg->moving || cfg->budget)
+    return bfail(b, LB_RT_EINVAL, "batched problems are static and keep no energy budget");
+  lb_rt_config c = *cfg;
+  c.storage = b->cfg.storage;
+  c.stream = b->stream;
+  c.budget = 0;
+  std::string err;
+  const size_t bytes = handle_device_bytes(c, err);
+  if (!bytes) return bfail(b, LB_RT_EINVAL, "invalid problem: " + err);
+  int s = -1;
+  for (int i = 0; i < (int)b->slots.size(); ++i)
+    if (!b->slots[i].used) {
+      s = i;
+      break;
+    }
+  if (s < 0) return bfail(b, LB_RT_EBUSY, "no free slot");
+  if (b->used + bytes > b->budget)
+    return bfail(b, LB_RT_EBUSY, "does not fit the memory budget now");
+  lb_rt* h = nullptr;
+  lb_rt_status st = lb_rt_create(&c, &h);
+  if (st != LB_RT_OK) return bfail(b, st, std::string("create: ") + lb_rt_last_error(nullptr));
+  if ((st = lb_rt_set_fluid(h, fluid, fluid_ptr_kind)) != LB_RT_OK ||
+      (st = lb_rt_set_state(h, state, state_kind, state_ptr_kind)) != LB_RT_OK) {
+    const std::string m = lb_rt_last_error(h);
+    lb_rt_destroy(h);
+    return bfail(b, st, m);
+  }
+  int gi = -1;
+  for (int i = 0; i < (int)b->groups.size(); ++i)
+    if (same_table(b->groups[i], h)) {
+      gi = i;
+      break;
+    }
+  if (gi < 0) {
+    Group g;
+    g.table = h->table;
+    g.Ni = h->Ni;
+    g.dpt = h->dpt;
+    g.zc = h->zc;
+    cudaError_t e = occupancy_static_batch(c.storage, g.dpt, g.zc, g.Ni / g.dpt, &g.per_sm);
+    if (e == cudaSuccess && g.per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) e = cudaEventCreate(&g.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g.ev1);
+    if (e != cudaSuccess) {
+      if (g.ev0) cudaEventDestroy(g.ev0);
+      lb_rt_destroy(h);
+      return bcuda(b, e, "batched kernel occupancy");
+    }
+    for (int z : kZCandidates) g.cands.push_back(z);
+    g.cost.assign(g.cands.size(), 0.0);
+    if (!b->cfg.autotune) g.tuned = true;
+    b->groups.push_back(g);
+    gi = (int)b->groups.size() - 1;
+  }
+  Member& m = b->slots[s];
+  m.h = h;
+  m.nsteps = nsteps;
+  m.bytes = bytes;
+  m.group = gi;
+  m.used = true;
+  b->used += bytes;
+  // tensor maps of both parities, copied to the device array at the next tick
+  for (int par = 0; par < 2; ++par) {
+    b->h_maps[(size_t)s * 4 + par * 2] = h->tmap[par];
+    if (c.storage != LB_RT_F32) b->h_maps[(size_t)s * 4 + par * 2 + 1] = h->emap[par];
+  }
+  b->maps_dirty = true;
+  *slot = s;
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
+  if (!b) return LB_RT_EINVAL;
+  const int K = b->cfg.steps_per_tick;
+  const int G = (int)b->groups.size();
+  // the previous tick must have read the staging tables
+  BCK(b, cudaStreamSynchronize(b->stream));
+  // plan[k][g]: slots of group g that take step k of this tick
+  std::vector<std::vector<std::vector<int>>> plan(K, std::vector<std::vector<int>>(G));
+  int active = 0;
+  std::vector<long long> group_sd(G, 0);
+  for (int s = 0; s < (int)b->slots.size(); ++s) {
+    const Member& m = b->slots[s];
+    if (!m.used) continue;
+    const long long rem = m.nsteps - m.h->steps;
+    if (rem <= 0) continue;
+    ++active;
+    const long long take = std::min<long long>(rem, K);
+    for (int k = 0; k < take; ++k) plan[k][m.group].push_back(s);
+    group_sd[m.group] += take * m.h->grid.sites;
+  }
+  if (n_active) *n_active = active;
+  if (!active) return LB_RT_OK;
+  // autotuner: a group whose member sites changed by more than 2x is retuned
+  bool tuning = false;
+  for (int g = 0; g < G; ++g) {
+    Group& gr = b->groups[g];
+    if (!group_sd[g]) continue;
+    long long sites = 0;
+    for (int s : plan[0][g]) sites += b->slots[s].h->grid.sites;
+    if (b->cfg.autotune && gr.tuned &&
+        (sites > 2 * gr.tuned_sites || 2 * sites < gr.tuned_sites)) {
+      gr.tuned = false;
+      gr.cand = 0;
+    }
+    if (!gr.tuned) {
+      gr.zchunk = gr.cands[gr.cand];
+      gr.tuned_sites = sites;
+      tuning = true;
+    }
+  }
+  // descriptor tables [step][group members]
+  size_t ndesc = 0;
+  for (int k = 0; k < K; ++k)
+    for (int g = 0; g < G; ++g) ndesc += plan[k][g].size();
+  if (ndesc > b->desc_cap) {
+    cudaFreeHost(b->h_desc);
+    cudaFree(b->d_desc);
+    b->h_desc = nullptr;
+    b->d_desc = nullptr;
+    b->desc_cap = 0;
+    b->graph_sig.clear();  // a captured graph refers to the old tables
+    const size_t cap = std::max<size_t>(ndesc, 2 * b->slots.size());
+    BCK(b, cudaMallocHost((void**)&b->h_desc, sizeof(ProblemDesc) * cap));
+    BCK(b, cudaMalloc((void**)&b->d_desc, sizeof(ProblemDesc) * cap));
+    b->desc_cap = cap;
+  }
+  std::vector<Launch> launches;
+  std::vector<long long> sig;
+  sig.push_back((long long)ndesc);
+  size_t at = 0;
+  for (int k = 0; k < K; ++k) {
+    for (int g = 0; g < G; ++g) {
+      const auto& ms = plan[k][g];
+      if (ms.empty()) continue;
+      const Group& gr = b->groups[g];
+      Launch L{g, (int)at, (int)ms.size(), 0};
+      for (int s : ms) {
+        const lb_rt* h = b->slots[s].h;
+        const int cur = (int)((h->cur + k) & 1);
+        ProblemDesc& d = b->h_desc[at++];
+        d = ProblemDesc{};
+        d.g = h->grid;
+        d.out = h->pop[cur ^ 1];
+        d.e_out = h->ef[cur ^ 1];
+        d.tmap = b->d_maps + (size_t)s * 4 + cur * 2;
+        d.emap = b->d_maps + (size_t)s * 4 + cur * 2 + 1;
+        d.cf = h->sc;
+        d.dt = (float)h->dt;
+        d.collision = h->cfg.collision;
+        d.lambda_iters = h->cfg.lambda_iters;
+        d.nzc = std::max(1, std::min(h->grid.nz, (h->grid.nz + gr.zchunk - 1) / gr.zchunk));
+        d.tile_start = L.ntiles;
+        d.ntiles = (h->grid.nx + 63) / 64 * h->grid.ny * d.nzc;
+        d.budget_partials = nullptr;
+        L.ntiles += d.ntiles;
+        sig.push_back(s);
+        sig.push_back(d.nzc);
+      }
+      launches.push_back(L);
+      sig.push_back(L.group);
+      sig.push_back(L.first);
+      sig.push_back(L.nprob);
+      sig.push_back(L.ntiles);
+    }
+  }
+  // the tick's device work: table uploads, then one batched launch per
+  // group and step
+  auto enqueue = [&](bool timed) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (b->maps_dirty || !timed)
+      e = cudaMemcpyAsync(b->d_maps, b->h_maps, sizeof(CUtensorMap) * 4 * b->slots.size(),
+                          cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(ProblemDesc) * ndesc,
+                          cudaMemcpyHostToDevice, b->stream);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+      Group& gr = b->groups[g];
+      const bool time_it = timed && !gr.tuned && group_sd[g] > 0;
+      if (time_it) e = cudaEventRecord(gr.ev0, b->stream);
+      for (const Launch& L : launches) {
+        if (L.group != g || e != cudaSuccess) continue;
+        BatchLaunch B{};
+        B.table = b->d_desc + L.first;
+        B.nprob = L.nprob;
+        B.ntiles = L.ntiles;
+        B.N = gr.Ni;
+        B.dpt = gr.dpt;
+        B.zc = gr.zc;
+        B.storage = b->cfg.storage;
+        B.ctas = (int)std::min<long long>((long long)gr.per_sm * b->sms, L.ntiles);
+        B.err = b->d_err;
+        gr.ctas = B.ctas;
+        e = launch_tma_static_batch(B, gr.table, b->stream);
+      }
+      if (e == cudaSuccess && time_it) e = cudaEventRecord(gr.ev1, b->stream);
+    }
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  if (tuning || !b->cfg.use_graph) {
+    e = enqueue(tuning);
+  } else {
+    // captured once per launch plan and replayed; the replay re-reads the
+    // staging tables, so only the plan (not the buffer parity) keys it
+    if (sig != b->graph_sig || !b->exec) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      b->graph_sig.clear();
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t e2 = enqueue(false);
+        e = cudaStreamEndCapture(b->stream, &b->graph);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e == cudaSuccess) b->graph_sig = sig;
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+  }
+  if (e != cudaSuccess) return bcuda(b, e, "batch tick");
+  b->maps_dirty = false;
+  // the members' step counters and buffer parity
+  for (int s = 0; s < (int)b->slots.size(); ++s) {
+    Member& m = b->slots[s];
+    if (!m.used) continue;
+    const long long rem = m.nsteps - m.h->steps;
+    if (rem <= 0) continue;
+    const long long take = std::min<long long>(rem, K);
+    m.h->cur ^= (int)(take & 1);
+    m.h->steps += take;
+  }
+  if (tuning) {
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int g = 0; g < G; ++g) {
+      Group& gr = b->groups[g];
+      if (gr.tuned || !group_sd[g]) continue;
+      float ms = 0.f;
+      BCK(b, cudaEventElapsedTime(&ms, gr.ev0, gr.ev1));
+      gr.cost[gr.cand] = ms / (double)group_sd[g];
+      if (++gr.cand == (int)gr.cands.size()) {
+        int best = 0;
+        for (int i = 1; i < (int)gr.cands.size(); ++i)
+          if (gr.cost[i] < gr.cost[best]) best = i;
+        gr.zchunk = gr.cands[best];
+        gr.tuned = true;
+      }
+    }
+  }
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_sync(lb_rt_batch* b) {
+  if (!b) return LB_RT_EINVAL;
+  BCK(b, cudaStreamSynchronize(b->stream));
+  unsigned word = 0;
+  BCK(b, cudaMemcpy(&word, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (word) return bfail(b, LB_RT_ETIMEDOUT, "device error word set by a batched step");
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_poll(lb_rt_batch* b, int* slots, int max, int* n) {
+  if (!b) return LB_RT_EINVAL;
+  if (!n || (max > 0 && !slots)) return bfail(b, LB_RT_EINVAL, "bad poll arguments");
+  int c = 0;
+  for (int s = 0; s < (int)b->slots.size(); ++s) {
+    const Member& m = b->slots[s];
+    if (m.used && m.h->steps >= m.nsteps) {
+      if (c < max) slots[c] = s;
+      ++c;
+    }
+  }
+  *n = std::min(c, max);
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_moments(lb_rt_batch* b, int slot, float* E, float* F, float* P,
+                                 int ptr_kind) {
+  if (!b) return LB_RT_EINVAL;
+  if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return bfail(b, LB_RT_EINVAL, "bad slot");
+  lb_rt* h = b->slots[slot].h;
+  const lb_rt_status st = lb_rt_moments(h, E, F, P, nullptr, ptr_kind);
+  if (st != LB_RT_OK) return bfail(b, st, lb_rt_last_error(h));
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_steps(const lb_rt_batch* b, int slot, long long* steps) {
+  if (!b || !steps || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return LB_RT_EINVAL;
+  *steps = b->slots[slot].h->steps;
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot) {
+  if (!b) return LB_RT_EINVAL;
+  if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return bfail(b, LB_RT_EINVAL, "bad slot");
+  BCK(b, cudaStreamSynchronize(b->stream));
+  Member& m = b->slots[slot];
+  lb_rt_destroy(m.h);
+  b->used -= m.bytes;
+  m = Member{};
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_tuning(const lb_rt_batch* b, int slot, int* zchunk, int* ctas) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used) return LB_RT_EINVAL;
+  const Group& g = b->groups[b->slots[slot].group];
+  if (zchunk) *zchunk = g.zchunk;
+  if (ctas) *ctas = g.ctas;
+  return LB_RT_OK;
+}
+
+const char* lb_rt_batch_last_error(const lb_rt_batch* b) { return b ? b->msg.c_str() : ""; }
+
+}  // extern "C"

@@ -7,53 +7,11 @@
 #include <cstring>
 #include <new>
 
+#include "handle.h"
 #include "lb_rt_internal.h"
 
 using namespace lbrt;
 
-struct lb_rt {
-  lb_rt_config cfg{};
-  Grid grid{};
-  int N = 0;                    // directions, external (user) order
-  int Ni = 0;                   // internal directions including inert padding
-  int dpt = 0, zc = 0;          // tile plan of the static kernel
-  int nzc = 0, ctas = 0;        // its persistent grid: z chunks, CTAs
-  std::vector<int> ext_of_int;  // internal -> external index (-1: padding)
-  std::vector<int> int_of_ext;  // external -> internal index
-  int* d_int_of_ext = nullptr;  // device copy
-  double dt = 0.0;
-  std::vector<double> n, w;
-  DirTable table{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  void* pop[2] = {nullptr, nullptr};
-  float* ef[2] = {nullptr, nullptr};   // 16-bit storage: padded E arrays paired with pop[]
-  size_t ef_bytes = 0;
-  CUtensorMap tmap[2];                 // TMA descriptors of pop[0] / pop[1]
-  CUtensorMap emap[2];                 // 16-bit storage: TMA descriptors of ef[0] / ef[1]
-  bool tmap_ok = false;
-  int cur = 0;
-  size_t pop_bytes = 0;
-  // coefficient fields: static ka, k0, lam, eta (slots 0-3); moving v(3), kta, kt0, etat (4-7)
-  float* fld[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  StaticCoef sc{};
-  MovingCoef mc{};
-  int64_t* frozen_cells = nullptr;
-  float* frozen_vals = nullptr;
-  int nfrozen = 0;
-  double* partials = nullptr;
-  int partials_cap = 0;
-  double* acc = nullptr;       // 8 doubles, see k_budget_finalize
-  unsigned* err = nullptr;     // device error word
-  float* scratch = nullptr;    // moments staging for host outputs [10][sites]
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  bool timing = false;
-  float last_ms = 0.f;
-  int last_nlaunch = 0;
-  long long steps = 0;
-  std::string msg;
-};
 
 namespace {
 
@@ -238,6 +196,30 @@ lb_rt_status reset_budget(lb_rt* h) {
 }
 
 }  // namespace
+
+size_t lbrt::handle_device_bytes(const lb_rt_config& cfg, std::string& err) {
+  lb_rt tmp;
+  tmp.cfg = cfg;
+  if (!build_directions(cfg, tmp.n, tmp.w, err)) return 0;
+  tmp.N = (int)tmp.w.size();
+  tmp.grid.nx = cfg.nx;
+  tmp.grid.ny = cfg.ny;
+  tmp.grid.nz = cfg.nz;
+  plan_directions(&tmp);
+  if (!cfg.moving && !tmp.dpt) {
+    err = "no tile plan fits this direction set";
+    return 0;
+  }
+  const size_t PX = ((size_t)(cfg.nx + GL + 1) + 7) / 8 * 8, PY = cfg.ny + 2, PZ = cfg.nz + 2;
+  const size_t sites = (size_t)cfg.nx * cfg.ny * cfg.nz;
+  size_t b = 2 * PX * PY * PZ * (size_t)tmp.Ni * elem_bytes(cfg.storage);
+  if (cfg.storage != LB_RT_F32) b += 2 * PX * PY * PZ * sizeof(float);
+  const size_t step_blocks = (size_t)((cfg.nx + 31) / 32) * cfg.ny * cfg.nz;
+  b += 2 * sizeof(double) * std::max<size_t>(4096, step_blocks);
+  b += (cfg.moving ? 6 : 4) * sites * sizeof(float);  // coefficient fields
+  b += 10 * sites * sizeof(float);                      // moments staging for host outputs
+  return b + 64 * 1024;
+}
 
 // Message for lb_rt_last_error(NULL) from a failed call that has no handle.
 void lbrt::set_unbound_error(const std::string& m) { g_create_msg = m; }

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "liblbrt.so")
 
 # constants of include/lb_rt.h
 LB_RT_OK, LB_RT_EINVAL, LB_RT_ENOMEM, LB_RT_ECUDA, LB_RT_ETIMEDOUT, LB_RT_ESTATE = 0, -1, -2, -3, -4, -5
+LB_RT_EBUSY = -6
+LB_RT_BATCH_MAX = 256
 LB_RT_RING2D, LB_RT_ICOSPHERE, LB_RT_GAUSS_LEGENDRE = 1, 2, 3
 LB_RT_PERIODIC, LB_RT_VACUUM = 0, 1
 LB_RT_F32, LB_RT_F16_DEV, LB_RT_BF16_DEV = 0, 1, 2
@@ -29,6 +31,9 @@ EXPORTED = [
     "lb_rt_restore_state", "lb_rt_sync", "lb_rt_directions", "lb_rt_enable_timing",
     "lb_rt_last_step_ms", "lb_rt_last_error", "lb_rt_version", "lb_rt_destroy",
     "lb_rt_total_energy_noalloc",
+    "lb_rt_batch_create", "lb_rt_batch_destroy", "lb_rt_batch_problem_bytes", "lb_rt_batch_admit",
+    "lb_rt_batch_tick", "lb_rt_batch_sync", "lb_rt_batch_poll", "lb_rt_batch_moments",
+    "lb_rt_batch_steps", "lb_rt_batch_release", "lb_rt_batch_tuning", "lb_rt_batch_last_error",
 ]
 
 
@@ -54,6 +59,12 @@ class lb_rt_fluid(C.Structure):
         ("kt_0", C.c_void_p), ("kt_0_s", C.c_float),
         ("eta_t", C.c_void_p), ("eta_t_s", C.c_float),
     ]
+
+
+class lb_rt_batch_config(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_problems", C.c_int), ("storage", C.c_int),
+                ("steps_per_tick", C.c_int), ("use_graph", C.c_int), ("autotune", C.c_int),
+                ("stream", C.c_void_p)]
 
 
 class lb_rt_budget(C.Structure):
@@ -103,6 +114,20 @@ def load(path=LIB_PATH):
         "lb_rt_destroy": (None, [H]),
         "lb_rt_total_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
                                                  C.c_int, C.c_void_p]),
+        "lb_rt_batch_create": (C.c_int, [C.POINTER(lb_rt_batch_config), C.POINTER(C.c_void_p)]),
+        "lb_rt_batch_destroy": (None, [H]),
+        "lb_rt_batch_problem_bytes": (C.c_size_t, [H, C.POINTER(lb_rt_config)]),
+        "lb_rt_batch_admit": (C.c_int, [H, C.POINTER(lb_rt_config), C.POINTER(lb_rt_fluid), C.c_int,
+                                        C.c_void_p, C.c_int, C.c_int, C.c_longlong,
+                                        C.POINTER(C.c_int)]),
+        "lb_rt_batch_tick": (C.c_int, [H, C.POINTER(C.c_int)]),
+        "lb_rt_batch_sync": (C.c_int, [H]),
+        "lb_rt_batch_poll": (C.c_int, [H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
+        "lb_rt_batch_moments": (C.c_int, [H, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+        "lb_rt_batch_steps": (C.c_int, [H, C.c_int, C.POINTER(C.c_longlong)]),
+        "lb_rt_batch_release": (C.c_int, [H, C.c_int]),
+        "lb_rt_batch_tuning": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "lb_rt_batch_last_error": (C.c_char_p, [H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -157,13 +182,11 @@ def _kind_of(objs):
 # entry points
 # ---------------------------------------------------------------------------
 
-def lb_rt_create(dims, nx, ny, nz=1, *, dirset=LB_RT_ICOSPHERE, ndir=0, level=1,
-                 gl=(0, 0), dirs=None, weights=None, ring_offset=0.0, cfl=0.5, dx=None,
+def _make_config(dims, nx, ny, nz=1, *, dirset=LB_RT_ICOSPHERE, ndir=0, level=1, gl=(0, 0),
+                 dirs=None, weights=None, ring_offset=0.0, cfl=0.5, dx=None,
                  bc=(LB_RT_PERIODIC,) * 3, storage=LB_RT_F32, collision=LB_RT_IMPLICIT_EXACT,
                  lambda_iters=1, moving=False, budget=False, stream=None):
-    """Create a handle (lb_rt_create).  `stream` is a cudaStream_t as an int
-    (e.g. torch.cuda.current_stream().cuda_stream) or None."""
-    lib = load()
+    """lb_rt_config from keyword arguments; returns (config, arrays to keep alive)."""
     cfg = lb_rt_config()
     cfg.dims, cfg.nx, cfg.ny, cfg.nz = dims, nx, ny, nz
     keep = []
@@ -192,6 +215,15 @@ def lb_rt_create(dims, nx, ny, nz=1, *, dirset=LB_RT_ICOSPHERE, ndir=0, level=1,
     cfg.storage, cfg.collision, cfg.lambda_iters = storage, collision, lambda_iters
     cfg.moving, cfg.budget = int(bool(moving)), int(bool(budget))
     cfg.stream = stream or None
+    return cfg, keep
+
+
+def lb_rt_create(dims, nx, ny, nz=1, **kw):
+    """Create a handle (lb_rt_create); keywords as _make_config.  `stream` is
+    a cudaStream_t as an int (e.g. torch.cuda.current_stream().cuda_stream)
+    or None."""
+    lib = load()
+    cfg, keep = _make_config(dims, nx, ny, nz, **kw)
     h = C.c_void_p()
     _check(None, lib.lb_rt_create(C.byref(cfg), C.byref(h)))
     return h
@@ -201,9 +233,10 @@ def lb_rt_destroy(h):
     load().lb_rt_destroy(h)
 
 
-def lb_rt_set_fluid(h, kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=None,
-                    kt_0=None, eta_t=None):
-    """Scalars or float32 site fields [nz, ny, nx] (v: [3, nz, ny, nx])."""
+def _make_fluid(kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=None, kt_0=None,
+                eta_t=None):
+    """lb_rt_fluid from scalars or float32 site fields; returns (fluid,
+    pointer kind, arrays to keep alive)."""
     f = lb_rt_fluid()
     arrays = []
 
@@ -234,7 +267,13 @@ def lb_rt_set_fluid(h, kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=
     put("kt_a", kt_a)
     put("kt_0", kt_0)
     put("eta_t", eta_t)
-    kind = _kind_of(arrays)
+    return f, _kind_of(arrays), arrays
+
+
+def lb_rt_set_fluid(h, kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=None,
+                    kt_0=None, eta_t=None):
+    """Scalars or float32 site fields [nz, ny, nx] (v: [3, nz, ny, nx])."""
+    f, kind, keep = _make_fluid(kappa_a, kappa_0, lam, eta, v, kt_a, kt_0, eta_t)
     _check(h, load().lb_rt_set_fluid(h, C.byref(f), kind))
 
 
@@ -341,3 +380,96 @@ def lb_rt_total_energy_noalloc(pop, ndir, sites, out=None, stream=None):
         raise ValueError("out must be a CUDA tensor")
     _check(None, lib.lb_rt_total_energy_noalloc(p, ndir, sites, op, LB_RT_DEVICE, stream or None))
     return out
+
+
+# ---- batch (many resident problems, one persistent launch per group) ----
+
+def _bcheck(b, st):
+    if st != LB_RT_OK:
+        msg = load().lb_rt_batch_last_error(b)
+        raise LBRTError(st, msg.decode() if msg else "")
+
+
+def lb_rt_batch_create(*, max_problems=64, storage=LB_RT_F16_DEV, steps_per_tick=10,
+                       mem_budget=0, use_graph=True, autotune=True, stream=None):
+    cfg = lb_rt_batch_config()
+    cfg.mem_budget, cfg.max_problems, cfg.storage = mem_budget, max_problems, storage
+    cfg.steps_per_tick, cfg.use_graph, cfg.autotune = steps_per_tick, int(use_graph), int(autotune)
+    cfg.stream = stream or None
+    b = C.c_void_p()
+    st = load().lb_rt_batch_create(C.byref(cfg), C.byref(b))
+    if st != LB_RT_OK:
+        raise LBRTError(st, "lb_rt_batch_create failed")
+    return b
+
+
+def lb_rt_batch_destroy(b):
+    load().lb_rt_batch_destroy(b)
+
+
+def lb_rt_batch_problem_bytes(b, dims, nx, ny, nz=1, **kw):
+    cfg, keep = _make_config(dims, nx, ny, nz, **kw)
+    return int(load().lb_rt_batch_problem_bytes(b, C.byref(cfg)))
+
+
+def lb_rt_batch_admit(b, problem, fluid, state, state_kind, nsteps):
+    """problem: keyword dict for _make_config (dims, nx, ny, nz, ...);
+    fluid: keyword dict for _make_fluid.  Returns the slot, or None when the
+    problem does not fit now (LB_RT_EBUSY)."""
+    p = dict(problem)
+    cfg, keep = _make_config(p.pop("dims"), p.pop("nx"), p.pop("ny"), p.pop("nz", 1), **p)
+    f, fkind, fkeep = _make_fluid(**fluid)
+    a = _f32(state)
+    sp, skind = _ptr(a)
+    slot = C.c_int(-1)
+    st = load().lb_rt_batch_admit(b, C.byref(cfg), C.byref(f), fkind, sp, state_kind, skind,
+                                  int(nsteps), C.byref(slot))
+    if st == LB_RT_EBUSY:
+        return None
+    _bcheck(b, st)
+    return slot.value
+
+
+def lb_rt_batch_tick(b):
+    n = C.c_int(0)
+    _bcheck(b, load().lb_rt_batch_tick(b, C.byref(n)))
+    return n.value
+
+
+def lb_rt_batch_sync(b):
+    _bcheck(b, load().lb_rt_batch_sync(b))
+
+
+def lb_rt_batch_poll(b, max_slots=LB_RT_BATCH_MAX):
+    arr = (C.c_int * max_slots)()
+    n = C.c_int(0)
+    _bcheck(b, load().lb_rt_batch_poll(b, arr, max_slots, C.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def lb_rt_batch_moments(b, slot, E=None, F=None, P=None):
+    kind = _kind_of([E, F, P])
+    _bcheck(b, load().lb_rt_batch_moments(b, slot, _ptr(E)[0], _ptr(F)[0], _ptr(P)[0], kind))
+
+
+def lb_rt_batch_steps(b, slot):
+    n = C.c_longlong(0)
+    _bcheck(b, load().lb_rt_batch_steps(b, slot, C.byref(n)))
+    return n.value
+
+
+def lb_rt_batch_release(b, slot):
+    _bcheck(b, load().lb_rt_batch_release(b, slot))
+
+
+def lb_rt_batch_tuning(b, slot):
+    z = C.c_int(0)
+    c = C.c_int(0)
+    _bcheck(b, load().lb_rt_batch_tuning(b, slot, C.byref(z), C.byref(c)))
+    return z.value, c.value
+
+
+def lb_rt_batch_last_error(b):
+    m = load().lb_rt_batch_last_error(b)
+    return m.decode() if m else ""
+
