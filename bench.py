@@ -215,6 +215,33 @@ def run_reference(args):
     return 0
 
 
+def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
+    """Batched serving on the seeded request stream (sphere/shadow, n in
+    {32..128}^3, 42 or 162 directions, kappa log-uniform 1e-1..1e4, 200-2000
+    steps, FP16 storage): capacity from a closed-loop run of the first
+    n_capacity requests (all present at t = 0), then the first n_open
+    requests with Poisson arrivals at 0.8 x that capacity."""
+    from paper_2007_05718_gb300 import serve
+    from paper_2007_05718_gb300 import workloads as W
+    closed = W.serving_requests(n_capacity, seed=seed, rate=1e9)
+    for r in closed:
+        r["arrival"] = 0.0
+    rc = serve.serve(closed, steps_per_tick=50, max_problems=64)
+    cap = rc["throughput_req_s"]
+    rate = 0.8 * cap
+    stream = W.serving_requests(n_open, seed=seed, rate=rate)
+    ro = serve.serve(stream, steps_per_tick=50, max_problems=64)
+    return {
+        "capacity_req_s": cap, "capacity_sd_s": rc["throughput_sd_s"],
+        "arrival_rate_req_s": rate, "requests": ro["requests"], "completed": ro["completed"],
+        "p50_s": ro["p50_s"], "p99_s": ro["p99_s"], "throughput_req_s": ro["throughput_req_s"],
+        "throughput_sd_s": ro["throughput_sd_s"], "max_concurrent": ro["max_concurrent"],
+        "storage": "fp16", "steps_per_tick": 50,
+        "sample": "first %d requests of the seed-%d stream (closed loop) and first %d with Poisson "
+                  "arrivals at 0.8 x capacity; the configured stream has 2000" % (n_capacity, seed, n_open),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +250,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -345,6 +373,11 @@ def main():
                 "ratio_vs_f32": ms_step / ms16,
                 "storage": "FP16 deviation from w_i E, float32 E per site, float32 arithmetic"},
     }
+    if not args.no_serving and ws == 1:
+        try:
+            line["serving"] = serving_measurement()
+        except Exception as e:  # report, do not hide
+            line["serving"] = {"error": str(e)[:300]}
     if not args.no_cpu_baseline:
         try:
             sec, sd = oracle_sample_time(64, 1)
