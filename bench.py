@@ -144,13 +144,21 @@ def _barrier(ws):
 
 
 def _max_over_ranks(ws, v):
+    """Maximum of a per-rank value over the replicas (NCCL on GPUs, gloo on CPU)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_step_per_rank, ws, ms_max, steps):
+    """Whole-job rate of N independent replicas: all ranks' units over the
+    slowest rank's time (weak scaling)."""
+    return units_per_step_per_rank * ws * steps / (ms_max * 1e-3)
 
 
 def _workload_fields():
@@ -300,7 +308,7 @@ def main():
         ms_max = _max_over_ranks(ws, ms)
         ms_step = ms_max / args.steps
         sd_step = sites * N
-        value = sd_step * ws / (ms_max * 1e-3 / args.steps)
+        value = aggregate_rate(sd_step, ws, ms_max, args.steps)
 
         # the same workload with FP16 populations (16-bit deviation storage)
         h16 = lbrt.lb_rt_create(3, N_SIDE, N_SIDE, N_SIDE, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL,
