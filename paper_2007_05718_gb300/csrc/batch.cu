@@ -94,7 +94,7 @@ bool same_table(const Group& g, const lb_rt* h) {
 }
 
 struct Launch {
-  int group, first, nprob, ntiles;
+  int group, first, nprob, ntiles, periodic;
 };
 
 }  // namespace
@@ -313,7 +313,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       const auto& ms = plan[k][g];
       if (ms.empty()) continue;
       const Group& gr = b->groups[g];
-      Launch L{g, (int)at, (int)ms.size(), 0};
+      Launch L{g, (int)at, (int)ms.size(), 0, 0};
       for (int s : ms) {
         const lb_rt* h = b->slots[s].h;
         const int cur = (int)((h->cur + k) & 1);
@@ -333,6 +333,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
         d.ntiles = (h->grid.nx + 63) / 64 * h->grid.ny * d.nzc;
         d.budget_partials = nullptr;
         L.ntiles += d.ntiles;
+        if (h->grid.periodic[0] || h->grid.periodic[1] || h->grid.periodic[2]) L.periodic = 1;
         sig.push_back(s);
         sig.push_back(d.nzc);
       }
@@ -341,6 +342,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       sig.push_back(L.first);
       sig.push_back(L.nprob);
       sig.push_back(L.ntiles);
+      sig.push_back(L.periodic);
     }
   }
   // the tick's device work: table uploads, then one batched launch per
@@ -368,6 +370,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
         B.zc = gr.zc;
         B.storage = b->cfg.storage;
         B.ctas = (int)std::min<long long>((long long)gr.per_sm * b->sms, L.ntiles);
+        B.periodic = L.periodic;
         B.err = b->d_err;
         gr.ctas = B.ctas;
         e = launch_tma_static_batch(B, gr.table, b->stream);

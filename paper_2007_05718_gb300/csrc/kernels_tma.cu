@@ -54,7 +54,10 @@ struct DirConst {
 // BATCH = false: one problem, `one` and `tmap1` in the parameter space.
 // BATCH = true: `table[nprob]` in device memory; each CTA copies the
 // descriptor of its current tile into shared memory.
-template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
+// PER: some problem of the launch has a periodic axis (ghost columns,
+// mirror rows and planes are written by the fast store path); all-vacuum
+// launches use the plain store loop.
+template <bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
            const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
@@ -336,35 +339,84 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
         c1z[j] = c[128];
       }
       bool zok[ZC], zface[ZC];
-      bool batch_plain = !y_face;
+      // the fast path writes one mirror row / plane at a periodic face; an
+      // extent of 1 on a periodic axis (two mirrors) takes the general path
+      bool batch_plain = !(y_face && ny == 1);
 #pragma unroll
       for (int j = 0; j < ZC; ++j) {
         const int z = zb + j;
         zok[j] = z >= zbeg && z < zend;
         zface[j] = gr.periodic[2] && (z == 0 || z == nz - 1);
-        batch_plain = batch_plain && zok[j] && !zface[j];
+        batch_plain = batch_plain && zok[j] && !(zface[j] && nz == 1);
       }
-      // fast path: every plane of the batch in the tile, no periodic-face
-      // images, every lane a full interior pair
-      const bool fast = __all_sync(0xffffffffu, in0 && in1 && !gx_lo && !gx_hi) && batch_plain;
-      if (alive && fast) {
-        float* base = orow + (long long)(zb + 1) * gr.sz;
+      // offsets (elements) of the mirror row / plane of a face row / plane
+      const int yface_rows = (y == ny - 1 ? 0 : ny + 1) - (y + 1);
+      // fast path: every plane of the batch in the tile, no periodic y/z
+      // face, every lane a full interior pair; a warp with a lane on a
+      // periodic x edge takes the variant that also writes the x ghost column
+      const bool fast = __all_sync(0xffffffffu, in0 && in1) && batch_plain;
+      const bool xghost = __any_sync(0xffffffffu, gx_lo || gx_hi);
+      bool done_fast = false;
+      if constexpr (!PER) {
+        if (alive && fast) {
+          // interior batch: one float2 store per direction and plane
+          float* base = orow + (long long)(zb + 1) * gr.sz;
 #pragma unroll
-        for (int k = 0; k < DPT; ++k) {
-          if (inert_mask >> k & 1u) continue;  // padding direction: its populations stay 0
-          const DirConst& d = dirs[i0 + k];
-          const float4 o0 = d.o0, o1 = d.o1;
-          const float2 w2 = make_float2(o0.x, o0.y), wx2 = make_float2(o0.z, o0.w);
-          const float2 wy2 = make_float2(o1.x, o1.y), wz2 = make_float2(o1.z, o1.w);
+          for (int k = 0; k < DPT; ++k) {
+            if (inert_mask >> k & 1u) continue;  // padding direction: its populations stay 0
+            const DirConst& d = dirs[i0 + k];
+            const float4 o0 = d.o0, o1 = d.o1;
+            const float2 w2 = make_float2(o0.x, o0.y), wx2 = make_float2(o0.z, o0.w);
+            const float2 wy2 = make_float2(o1.x, o1.y), wz2 = make_float2(o1.z, o1.w);
 #pragma unroll
-          for (int j = 0; j < ZC; ++j) {
-            const float2 eq =
-                f2fma(wz2, c1z[j], f2fma(wy2, c1y[j], f2fma(wx2, c1x[j], f2mul(w2, c0[j]))));
-            *reinterpret_cast<float2*>(base + (long long)k * gr.si + (long long)j * gr.sz) =
-                f2fma(al[j], Is[k][j], eq);
+            for (int j = 0; j < ZC; ++j) {
+              const float2 eq =
+                  f2fma(wz2, c1z[j], f2fma(wy2, c1y[j], f2fma(wx2, c1x[j], f2mul(w2, c0[j]))));
+              *reinterpret_cast<float2*>(base + (long long)k * gr.si + (long long)j * gr.sz) =
+                  f2fma(al[j], Is[k][j], eq);
+            }
           }
+          done_fast = true;
         }
-      } else if (alive && in0) {
+      } else {
+        if (alive && fast) {
+          // periodic edges: the same stores plus the x ghost column and one
+          // mirror row / plane image
+          float* base = orow + (long long)(zb + 1) * gr.sz;
+#pragma unroll
+          for (int k = 0; k < DPT; ++k) {
+            if (inert_mask >> k & 1u) continue;
+            const DirConst& d = dirs[i0 + k];
+            const float4 o0 = d.o0, o1 = d.o1;
+            const float2 w2 = make_float2(o0.x, o0.y), wx2 = make_float2(o0.z, o0.w);
+            const float2 wy2 = make_float2(o1.x, o1.y), wz2 = make_float2(o1.z, o1.w);
+#pragma unroll
+            for (int j = 0; j < ZC; ++j) {
+              const float2 eq =
+                  f2fma(wz2, c1z[j], f2fma(wy2, c1y[j], f2fma(wx2, c1x[j], f2mul(w2, c0[j]))));
+              const float2 o = f2fma(al[j], Is[k][j], eq);
+              float* dst = base + (long long)k * gr.si + (long long)j * gr.sz;
+              auto put = [&](float* dd) {
+                *reinterpret_cast<float2*>(dd) = o;
+                if (xghost) {  // warp-uniform
+                  if (gx_lo) dd[GL - 1 - (xa + GL)] = lo_from_y ? o.y : o.x;
+                  if (gx_hi) dd[nx + GL - (xa + GL)] = o.x;
+                }
+              };
+              put(dst);
+              if (y_face) put(dst + (long long)yface_rows * gr.sy);  // warp-uniform
+              if (zface[j]) {
+                const int z = zb + j;
+                const long long zd = (long long)((z == nz - 1 ? 0 : nz + 1) - (z + 1)) * gr.sz;
+                put(dst + zd);
+                if (y_face) put(dst + zd + (long long)yface_rows * gr.sy);
+              }
+            }
+          }
+          done_fast = true;
+        }
+      }
+      if (!done_fast && alive && in0) {
 #pragma unroll
         for (int k = 0; k < DPT; ++k) {
           if (inert_mask >> k & 1u) continue;
@@ -441,27 +493,38 @@ size_t step_smem(int G) {
          sizeof(DirConst) * (size_t)G * DPT + 8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
 }
 
-template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
+template <bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr() {
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<BATCH, DPT, ZC, R, MAXT, REGS>,
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<BATCH, PER, DPT, ZC, R, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
   return e;
 }
 
+// Resident CTAs per SM; the two boundary specialisations have the same
+// launch bounds and shared memory, the smaller count is returned.
 template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy(int G, int* per_sm) {
-  cudaError_t e = set_smem_attr<BATCH, DPT, ZC, R, MAXT, REGS>();
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      per_sm, k_step_f32<BATCH, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  int a = 0, b = 0;
+  cudaError_t e = set_smem_attr<BATCH, false, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_smem_attr<BATCH, true, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_f32<BATCH, false, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_f32<BATCH, true, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  *per_sm = std::min(a, b);
+  return e;
 }
+
+bool any_periodic(const Grid& g) { return g.periodic[0] || g.periodic[1] || g.periodic[2]; }
 
 template <int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
@@ -474,7 +537,9 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   if (nblocks) *nblocks = L.ctas;
   const size_t smem = step_smem<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr<false, DPT, ZC, R, MAXT, REGS>();
+  const bool per = any_periodic(L.g);
+  const cudaError_t e = per ? set_smem_attr<false, true, DPT, ZC, R, MAXT, REGS>()
+                            : set_smem_attr<false, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   ProblemDesc one{};
   one.g = L.g;
@@ -488,8 +553,12 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   one.tile_start = 0;
   one.ntiles = (L.g.nx + 63) / 64 * L.g.ny * L.nzc;
   one.budget_partials = L.budget_partials;
-  k_step_f32<false, DPT, ZC, R, MAXT, REGS>
-      <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
+  if (per)
+    k_step_f32<false, true, DPT, ZC, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
+  else
+    k_step_f32<false, false, DPT, ZC, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
   return cudaGetLastError();
 }
 
@@ -501,13 +570,18 @@ cudaError_t launch_f32_batch(const BatchLaunch& B, const DirTable& t, cudaStream
     return cudaErrorInvalidValue;
   const size_t smem = step_smem<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr<true, DPT, ZC, R, MAXT, REGS>();
+  const cudaError_t e = B.periodic ? set_smem_attr<true, true, DPT, ZC, R, MAXT, REGS>()
+                                   : set_smem_attr<true, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   // the parameter-space tensor map and descriptor are unused by the batched kernel
   CUtensorMap unused{};
   ProblemDesc none{};
-  k_step_f32<true, DPT, ZC, R, MAXT, REGS>
-      <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
+  if (B.periodic)
+    k_step_f32<true, true, DPT, ZC, R, MAXT, REGS>
+        <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
+  else
+    k_step_f32<true, false, DPT, ZC, R, MAXT, REGS>
+        <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   return cudaGetLastError();
 }
 

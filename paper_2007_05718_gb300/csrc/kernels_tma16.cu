@@ -84,7 +84,9 @@ __device__ __forceinline__ void store_e(float* e, const Grid& g, int z, int y, i
 
 // BATCH as in the float32 kernel: one problem in the parameter space, or a
 // device array of problem descriptors walked by the persistent CTAs.
-template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
+// PER as in the float32 kernel: periodic axes take the fast store path
+// that also writes ghost columns and mirror rows / planes.
+template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUtensorMap emap1,
           const __grid_constant__ ProblemDesc one, const ProblemDesc* __restrict__ table,
@@ -411,32 +413,78 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
         c1z[j] = c[128];
       }
       bool zok[ZC], zface[ZC];
-      bool batch_plain = !y_face;
+      // the fast path writes one mirror row / plane at a periodic face; an
+      // extent of 1 on a periodic axis (two mirrors) takes the general path
+      bool batch_plain = !(y_face && ny == 1);
 #pragma unroll
       for (int j = 0; j < ZC; ++j) {
         const int z = zb + j;
         zok[j] = z >= zbeg && z < zend;
         zface[j] = gr.periodic[2] && (z == 0 || z == nz - 1);
-        batch_plain = batch_plain && zok[j] && !zface[j];
+        batch_plain = batch_plain && zok[j] && !(zface[j] && nz == 1);
       }
-      const bool fast = __all_sync(0xffffffffu, in0 && in1 && !gx_lo && !gx_hi) && batch_plain;
-      if (alive && fast) {
-        ST* base = orow + (long long)(zb + 1) * gr.sz;
+      // offsets (elements) of the mirror row / plane of a face row / plane
+      const int yface_rows = (y == ny - 1 ? 0 : ny + 1) - (y + 1);
+      // a warp with a lane on a periodic x edge also writes the x ghost column
+      const bool fast = __all_sync(0xffffffffu, in0 && in1) && batch_plain;
+      const bool xghost = __any_sync(0xffffffffu, gx_lo || gx_hi);
+      bool done_fast = false;
+      if constexpr (!PER) {
+        if (alive && fast) {
+          ST* base = orow + (long long)(zb + 1) * gr.sz;
 #pragma unroll
-        for (int k = 0; k < DPT; ++k) {
-          if (inert_mask >> k & 1u) continue;
-          const DirConst16& d = dirs[i0 + k];
-          const float4 s1 = d.s1, s2 = d.s2;
-          const float2 nx2 = make_float2(s1.z, s1.w);
-          const float2 ny2 = make_float2(s2.x, s2.y), nz2 = make_float2(s2.z, s2.w);
+          for (int k = 0; k < DPT; ++k) {
+            if (inert_mask >> k & 1u) continue;
+            const DirConst16& d = dirs[i0 + k];
+            const float4 s1 = d.s1, s2 = d.s2;
+            const float2 nx2 = make_float2(s1.z, s1.w);
+            const float2 ny2 = make_float2(s2.x, s2.y), nz2 = make_float2(s2.z, s2.w);
 #pragma unroll
-          for (int j = 0; j < ZC; ++j) {
-            const float2 qn =
-                f2fma(al[j], Is[k][j], f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j]))));
-            *reinterpret_cast<T2*>(base + (long long)k * gr.si + (long long)j * gr.sz) = C2::from2(qn);
+            for (int j = 0; j < ZC; ++j) {
+              const float2 qn =
+                  f2fma(al[j], Is[k][j], f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j]))));
+              *reinterpret_cast<T2*>(base + (long long)k * gr.si + (long long)j * gr.sz) = C2::from2(qn);
+            }
           }
+          done_fast = true;
         }
-      } else if (alive && in0) {
+      } else {
+        if (alive && fast) {
+          ST* base = orow + (long long)(zb + 1) * gr.sz;
+#pragma unroll
+          for (int k = 0; k < DPT; ++k) {
+            if (inert_mask >> k & 1u) continue;
+            const DirConst16& d = dirs[i0 + k];
+            const float4 s1 = d.s1, s2 = d.s2;
+            const float2 nx2 = make_float2(s1.z, s1.w);
+            const float2 ny2 = make_float2(s2.x, s2.y), nz2 = make_float2(s2.z, s2.w);
+#pragma unroll
+            for (int j = 0; j < ZC; ++j) {
+              const float2 qn =
+                  f2fma(al[j], Is[k][j], f2fma(nz2, c1z[j], f2fma(ny2, c1y[j], f2fma(nx2, c1x[j], c0[j]))));
+              ST* dst = base + (long long)k * gr.si + (long long)j * gr.sz;
+              const T2 h = C2::from2(qn);
+              auto put = [&](ST* d) {
+                *reinterpret_cast<T2*>(d) = h;
+                if (xghost) {  // warp-uniform
+                  if (gx_lo) d[GL - 1 - (xa + GL)] = lo_from_y ? h.y : h.x;
+                  if (gx_hi) d[nx + GL - (xa + GL)] = h.x;
+                }
+              };
+              put(dst);
+              if (y_face) put(dst + (long long)yface_rows * gr.sy);  // warp-uniform
+              if (zface[j]) {
+                const int z = zb + j;
+                const long long zd = (long long)((z == nz - 1 ? 0 : nz + 1) - (z + 1)) * gr.sz;
+                put(dst + zd);
+                if (y_face) put(dst + zd + (long long)yface_rows * gr.sy);
+              }
+            }
+          }
+          done_fast = true;
+        }
+      }
+      if (!done_fast && alive && in0) {
 #pragma unroll
         for (int k = 0; k < DPT; ++k) {
           if (inert_mask >> k & 1u) continue;
@@ -505,13 +553,13 @@ size_t step_smem16(int G) {
          sizeof(DirConst16) * (size_t)G * DPT + 8 * ((size_t)G * R + R) + sizeof(double) * 4 * ZC + 16;
 }
 
-template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
+template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr16() {
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_16<ST, BATCH, DPT, ZC, R, MAXT, REGS>,
+  const cudaError_t e = cudaFuncSetAttribute(k_step_16<ST, BATCH, PER, DPT, ZC, R, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
@@ -520,10 +568,19 @@ cudaError_t set_smem_attr16() {
 
 template <class ST, bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy16(int G, int* per_sm) {
-  cudaError_t e = set_smem_attr16<ST, BATCH, DPT, ZC, R, MAXT, REGS>();
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      per_sm, k_step_16<ST, BATCH, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem16<DPT, ZC, R>(G));
+  int a = 0, b = 0;
+  cudaError_t e = set_smem_attr16<ST, BATCH, false, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_smem_attr16<ST, BATCH, true, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_16<ST, BATCH, false, DPT, ZC, R, MAXT, REGS>, 32 * G,
+        step_smem16<DPT, ZC, R>(G));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_16<ST, BATCH, true, DPT, ZC, R, MAXT, REGS>, 32 * G,
+        step_smem16<DPT, ZC, R>(G));
+  *per_sm = std::min(a, b);
+  return e;
 }
 
 template <class ST, int DPT, int ZC, int R, int MAXT, int REGS>
@@ -537,7 +594,9 @@ cudaError_t launch16(const StepLaunch& L, const StaticCoef& c, const DirTable& t
   if (nblocks) *nblocks = L.ctas;
   const size_t smem = step_smem16<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr16<ST, false, DPT, ZC, R, MAXT, REGS>();
+  const bool per = L.g.periodic[0] || L.g.periodic[1] || L.g.periodic[2];
+  const cudaError_t e = per ? set_smem_attr16<ST, false, true, DPT, ZC, R, MAXT, REGS>()
+                            : set_smem_attr16<ST, false, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   ProblemDesc one{};
   one.g = L.g;
@@ -551,8 +610,12 @@ cudaError_t launch16(const StepLaunch& L, const StaticCoef& c, const DirTable& t
   one.tile_start = 0;
   one.ntiles = (L.g.nx + 63) / 64 * L.g.ny * L.nzc;
   one.budget_partials = L.budget_partials;
-  k_step_16<ST, false, DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(
-      *L.tmap_in, *L.tmap_e, one, nullptr, 1, one.ntiles, L.err, t);
+  if (per)
+    k_step_16<ST, false, true, DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(
+        *L.tmap_in, *L.tmap_e, one, nullptr, 1, one.ntiles, L.err, t);
+  else
+    k_step_16<ST, false, false, DPT, ZC, R, MAXT, REGS><<<L.ctas, dim3(32, G), smem, s>>>(
+        *L.tmap_in, *L.tmap_e, one, nullptr, 1, one.ntiles, L.err, t);
   return cudaGetLastError();
 }
 
@@ -564,12 +627,17 @@ cudaError_t launch16_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t
     return cudaErrorInvalidValue;
   const size_t smem = step_smem16<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = set_smem_attr16<ST, true, DPT, ZC, R, MAXT, REGS>();
+  const cudaError_t e = B.periodic ? set_smem_attr16<ST, true, true, DPT, ZC, R, MAXT, REGS>()
+                                   : set_smem_attr16<ST, true, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   CUtensorMap unused{};
   ProblemDesc none{};
-  k_step_16<ST, true, DPT, ZC, R, MAXT, REGS><<<B.ctas, dim3(32, G), smem, s>>>(
-      unused, unused, none, B.table, B.nprob, B.ntiles, B.err, t);
+  if (B.periodic)
+    k_step_16<ST, true, true, DPT, ZC, R, MAXT, REGS><<<B.ctas, dim3(32, G), smem, s>>>(
+        unused, unused, none, B.table, B.nprob, B.ntiles, B.err, t);
+  else
+    k_step_16<ST, true, false, DPT, ZC, R, MAXT, REGS><<<B.ctas, dim3(32, G), smem, s>>>(
+        unused, unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   return cudaGetLastError();
 }
 

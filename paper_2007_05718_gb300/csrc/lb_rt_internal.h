@@ -119,6 +119,7 @@ struct BatchLaunch {
   int nprob, ntiles;         // problems, total tiles
   int N, dpt, zc, storage;
   int ctas;
+  int periodic;              // some problem has a periodic axis
   unsigned* err;
 };
 cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
