@@ -10,6 +10,8 @@
 // per-direction collision terms in registers; the per-site sums of the G
 // groups meet in shared memory and the site-local implicit collision is
 // closed-form.
+#include <type_traits>
+
 #include "lb_rt_internal.h"
 
 namespace lbrt {
@@ -48,6 +50,59 @@ __device__ __forceinline__ float pull(const float* __restrict__ p, const Grid& g
   return fmaf(az, r1 - r0, r0);
 }
 
+// 16-bit storage (f_i = I_i / w_i = E^ (1 + q_i), E^ in a padded float32
+// array): the streamed f*_i of Eq. (interp) from the decoded corners.  `q`
+// points at q_i(r), `e` at E^(r).
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class ST>
+__device__ __forceinline__ float pull16(const ST* __restrict__ q, const float* __restrict__ e,
+                                        const Grid& g, float4 au) {
+  const int oct = __float_as_int(au.w);
+  const long long dxo = (oct & 1) ? 1 : -1;
+  const long long dyo = (oct & 2) ? g.sy : -g.sy;
+  const long long dzo = (oct & 4) ? g.sz : -g.sz;
+  const long long eyo = (oct & 2) ? g.PX : -(long long)g.PX;
+  const long long ezo = (oct & 4) ? (long long)g.PX * g.PY : -(long long)g.PX * g.PY;
+  auto f = [&](long long dq, long long de) {
+    const float E = __ldg(e + de);
+    return fmaf(E, to_f32(q[dq]), E);
+  };
+  const float ax = au.x, ay = au.y, az = au.z;
+  const float v000 = f(0, 0), v100 = f(dxo, dxo), v010 = f(dyo, eyo), v110 = f(dxo + dyo, dxo + eyo);
+  const float b0 = fmaf(ax, v100 - v000, v000);
+  const float b1 = fmaf(ax, v110 - v010, v010);
+  const float r0 = fmaf(ay, b1 - b0, b0);
+  if (az == 0.f) return r0;
+  const float v001 = f(dzo, ezo), v101 = f(dzo + dxo, ezo + dxo), v011 = f(dzo + dyo, ezo + eyo),
+              v111 = f(dzo + dxo + dyo, ezo + dxo + eyo);
+  const float c0 = fmaf(ax, v101 - v001, v001);
+  const float c1 = fmaf(ax, v111 - v011, v011);
+  const float r1 = fmaf(ay, c1 - c0, c0);
+  return fmaf(az, r1 - r0, r0);
+}
+
+template <class ST> __device__ __forceinline__ ST from_f32(float v);
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// E^ of a site into the padded E array and its periodic mirrors.
+__device__ __forceinline__ void store_e_mirrored(float* e, const Grid& g, int z, int y, int x,
+                                                 float v) {
+  int xs[3], ys[3], zs[3];
+  const int nxs = mirrors(x, g.nx, g.periodic[0], GL, xs);
+  const int nys = mirrors(y, g.ny, g.periodic[1], 1, ys);
+  const int nzs = mirrors(z, g.nz, g.periodic[2], 1, zs);
+  for (int a = 0; a < nzs; ++a)
+    for (int b = 0; b < nys; ++b)
+      for (int c = 0; c < nxs; ++c)
+        e[(long long)zs[a] * g.PX * g.PY + (long long)ys[b] * g.PX + xs[c]] = v;
+}
+
 __device__ __forceinline__ float field(const float* __restrict__ p, float s, long long i) {
   return p ? __ldg(p + i) : s;
 }
@@ -73,9 +128,12 @@ __device__ __forceinline__ void budget_add(double* partials, double a, double b)
 //   I_i^{n+1} = A_i I*_i + g_i (eta_t + kt_0 J),
 //   J = W^2 sum beta_i^2 I_i^{n+1} = X / (1 - Y),
 //   X = W^2 sum beta_i^2 (A_i I*_i + g_i eta_t),  Y = kt_0 W^2 sum beta_i^2 g_i.
-template <int DPT>
+// ST = float: populations I_i; ST = __half / __nv_bfloat16: the 16-bit
+// deviation form, decoded at the corners and encoded against the site's new
+// energy density E' = sum_i I_i^{n+1} = sum_i A_i I*_i + (eta_t + kt_0 J) sum_i g_i.
+template <class ST, int DPT>
 __global__ void __launch_bounds__(32 * TY * 4)
-k_step_moving_f32(const StepLaunch L, const MovingCoef cf, const DirTable t) {
+k_step_moving(const StepLaunch L, const MovingCoef cf, const DirTable t) {
   extern __shared__ float4 red[];  // [2][G][TY*32]
   const int G = blockDim.z;
   const int tx = threadIdx.x, ty = threadIdx.y, g = threadIdx.z;
@@ -85,8 +143,9 @@ k_step_moving_f32(const StepLaunch L, const MovingCoef cf, const DirTable t) {
   const int xs = valid ? x : 0, ys = valid ? y : 0;
   const long long site = ((long long)z * gr.ny + ys) * gr.nx + xs;
   const long long sites = gr.sites;
-  const float* __restrict__ in = static_cast<const float*>(L.in);
-  float* __restrict__ out = static_cast<float*>(L.out);
+  const ST* __restrict__ in = static_cast<const ST*>(L.in);
+  ST* __restrict__ out = static_cast<ST*>(L.out);
+  constexpr bool F32 = std::is_same<ST, float>::value;
 
   float vx = 0.f, vy = 0.f, vz = 0.f;
   if (cf.v) {
@@ -111,7 +170,13 @@ k_step_moving_f32(const StepLaunch L, const MovingCoef cf, const DirTable t) {
     gi[k] = 0.f;
     if (k < nd) {
       const float4 nw = t.nw[i0 + k];
-      const float r = pull(in + pidx(gr, i0 + k, z, ys, xs), gr, t.au[i0 + k]);
+      float r;
+      if constexpr (F32) {
+        r = pull(in + pidx(gr, i0 + k, z, ys, xs), gr, t.au[i0 + k]);
+      } else {
+        const long long ei = (long long)(z + 1) * gr.PX * gr.PY + (long long)(ys + 1) * gr.PX + xs + GL;
+        r = nw.w * pull16(in + pidx(gr, i0 + k, z, ys, xs), L.e_in + ei, gr, t.au[i0 + k]);
+      }
       const float beta = 1.f - fmaf(vx, nw.x, fmaf(vy, nw.y, vz * nw.z));
       const float Wb = W * beta;
       const float A = 1.f / fmaf(dt * Wb, ksum, 1.f);
@@ -143,12 +208,21 @@ k_step_moving_f32(const StepLaunch L, const MovingCoef cf, const DirTable t) {
   const float src = fmaf(kt0, J, etat);
   if (valid) {
     const bool mirror = has_mirror(gr, z, y, x);
+    float rinv = 0.f;
+    if constexpr (!F32) {
+      const float Eh = fmaxf(fmaf(s2, src, m.w), 1e-30f);
+      rinv = __fdividef(1.f, Eh);
+      if (g == 0) store_e_mirrored(L.e_out, gr, z, y, x, Eh);
+    }
 #pragma unroll
     for (int k = 0; k < DPT; ++k) {
       if (k < nd) {
         const float o = fmaf(gi[k], src, AI[k]);
-        if (mirror) store_pop(out, gr, i0 + k, z, y, x, o);
-        else out[pidx(gr, i0 + k, z, y, x)] = o;
+        ST v;
+        if constexpr (F32) v = o;
+        else v = from_f32<ST>(fmaf(__fdividef(o, t.nw[i0 + k].w), rinv, -1.f));
+        if (mirror) store_pop(out, gr, i0 + k, z, y, x, v);
+        else out[pidx(gr, i0 + k, z, y, x)] = v;
       }
     }
   }
@@ -157,7 +231,7 @@ k_step_moving_f32(const StepLaunch L, const MovingCoef cf, const DirTable t) {
                valid ? (double)fmaf(s2, src, m.w) : 0.0);
 }
 
-template <int DPT>
+template <class ST, int DPT>
 cudaError_t launch_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t, int G,
                           cudaStream_t s, int* nblocks) {
   dim3 block(32, TY, G);
@@ -165,7 +239,8 @@ cudaError_t launch_moving(const StepLaunch& L, const MovingCoef& c, const DirTab
   const long long nb_ = (long long)grid.x * grid.y * grid.z;
   if (L.budget_partials && nb_ > L.partials_cap) return cudaErrorInvalidValue;
   if (nblocks) *nblocks = (int)nb_;
-  k_step_moving_f32<DPT><<<grid, block, sizeof(float4) * 2 * G * TY * 32, s>>>(L, c, t);
+  if (!std::is_same<ST, float>::value && (!L.e_in || !L.e_out)) return cudaErrorInvalidValue;
+  k_step_moving<ST, DPT><<<grid, block, sizeof(float4) * 2 * G * TY * 32, s>>>(L, c, t);
   return cudaGetLastError();
 }
 
@@ -179,14 +254,20 @@ cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const D
 
 cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks) {
-  if (storage != ST_F32) return cudaErrorNotSupported;
   const int N = L.N;
   const int G = (N + 47) / 48;
   if (G > 4 || N < 1) return cudaErrorInvalidValue;
   const int per = (N + G - 1) / G;
-  if (per <= 16) return launch_moving<16>(L, c, t, G, s, nblocks);
-  if (per <= 32) return launch_moving<32>(L, c, t, G, s, nblocks);
-  return launch_moving<48>(L, c, t, G, s, nblocks);
+  auto go = [&](auto tag) {
+    using ST = decltype(tag);
+    if (per <= 16) return launch_moving<ST, 16>(L, c, t, G, s, nblocks);
+    if (per <= 32) return launch_moving<ST, 32>(L, c, t, G, s, nblocks);
+    return launch_moving<ST, 48>(L, c, t, G, s, nblocks);
+  };
+  if (storage == ST_F32) return go(float());
+  if (storage == ST_F16) return go(__half());
+  if (storage == ST_BF16) return go(__nv_bfloat16());
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lbrt

@@ -254,8 +254,6 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   if (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
       cfg->storage != LB_RT_BF16_DEV)
     return bad("bad storage");
-  if (cfg->storage != LB_RT_F32 && cfg->moving)
-    return bad("16-bit storage with a moving fluid is not available yet");
   if (cfg->collision != LB_RT_IMPLICIT_EXACT && cfg->collision != LB_RT_EXPLICIT &&
       cfg->collision != LB_RT_LAMBDA_K)
     return bad("bad collision");
@@ -517,6 +515,7 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
     L.out = h->pop[h->cur ^ 1];
     L.tmap_in = h->tmap_ok ? &h->tmap[h->cur] : nullptr;
     L.tmap_e = h->ef[0] && h->tmap_ok ? &h->emap[h->cur] : nullptr;
+    L.e_in = h->ef[h->cur];
     L.e_out = h->ef[h->cur ^ 1];
     L.err = h->err;
     L.budget_partials = nullptr;

@@ -87,6 +87,7 @@ struct StepLaunch {
   void* out;           // populations at t + dt
   const CUtensorMap* tmap_in;  // TMA descriptor of `in` (host copy)
   const CUtensorMap* tmap_e;   // 16-bit storage: TMA descriptor of the E array at t
+  const float* e_in;           // 16-bit storage: E array at t (padded, float32)
   float* e_out;                // 16-bit storage: E array at t + dt (padded, float32)
   double* budget_partials;  // [nblocks][2] (sum E*, sum E_collided) or nullptr
   long long partials_cap;   // slots available; a launcher whose grid is larger refuses

@@ -160,3 +160,31 @@ def test_frozen_beam_injection(cuda, storage):
     p = Problem(2, (1, ny, nx), "ring", ndir=N, cfl=0.2, bc="vpp", storage=storage,
                 state=state, frozen=(cells, vals), budget=True)
     _check(p, 60)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("level", [1, 2])
+def test_moving_shear_reduced(cuda, storage, level):
+    """Moving background (App. B) with 16-bit storage: the shear-flow
+    generator on a 20^3 periodic box, smooth initial E and F (P1 state)."""
+    n = 20
+    mf = W.moving_fluid(n)
+    shape = (n, n, n)
+    E0 = 1.0 + W.smooth_field(shape, 41).astype(np.float32)
+    F0 = 0.2 * np.stack([W.smooth_field(shape, 42 + k) for k in range(3)]).astype(np.float32)
+    p = Problem(3, shape, "ico", level=level, storage=storage,
+                moving=dict(v=mf["v"], kt_a=mf["kt_a"], kt_0=mf["kt_0"], eta_t=mf["eta_t"]),
+                state_kind=lbrt.LB_RT_STATE_P1, state=np.concatenate([E0[None], F0]), budget=True)
+    _check(p, 12)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_moving_with_vacuum_faces(cuda, storage):
+    shape = (6, 9, 35)
+    v = 0.4 * np.stack([W.smooth_field(shape, 51 + k) for k in range(3)]).astype(np.float32) / 3.0
+    p = Problem(3, shape, "ico", level=1, bc="vpv", storage=storage,
+                moving=dict(v=v, kt_a=W.random_fields(shape, 55, 0.0, 10.0),
+                            kt_0=W.random_fields(shape, 56, 0.0, 20.0), eta_t=1.0),
+                state_kind=lbrt.LB_RT_STATE_ISOTROPIC,
+                state=(1.0 + 0.5 * W.smooth_field(shape, 57)).astype(np.float32))
+    _check(p, 8, f_scale="E")
