@@ -223,6 +223,72 @@ def run_reference(args):
     return 0
 
 
+def collision_mode_costs(steps=20, warmup=3, n=128):
+    """Step time of the three collision forms on one workload (128^3 x 42,
+    periodic, kappa_a = 1, kappa_0 = 1e3, lambda = 0.5, eta = 1, FP32): the
+    exact implicit closed form, the explicit update and the paper's
+    Lambda iteration with 5 cycles (its timing runs use 5)."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    E0 = torch.from_numpy(W.gaussian_E0((n, n, n), 8.0)).cuda()
+    out = {}
+    for name, coll, iters in (("implicit_exact", lbrt.LB_RT_IMPLICIT_EXACT, 1),
+                              ("explicit", lbrt.LB_RT_EXPLICIT, 1),
+                              ("lambda_5", lbrt.LB_RT_LAMBDA_K, 5)):
+        stream = torch.cuda.Stream()
+        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=1, cfl=CFL,
+                              collision=coll, lambda_iters=iters, stream=stream.cuda_stream)
+        lbrt.lb_rt_set_fluid(h, kappa_a=1.0, kappa_0=1000.0, lam=0.5, eta=1.0)
+        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        lbrt.lb_rt_step(h, warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lbrt.lb_rt_step(h, steps)
+        b.record(stream)
+        b.synchronize()
+        out[name + "_ms"] = a.elapsed_time(b) / steps
+        lbrt.lb_rt_destroy(h)
+    out["implicit_over_explicit"] = out["implicit_exact_ms"] / out["explicit_ms"]
+    out["lambda5_over_explicit"] = out["lambda_5_ms"] / out["explicit_ms"]
+    out["workload"] = "128^3 x 42 periodic, kappa_a 1, kappa_0 1e3, lambda 0.5, eta 1, FP32"
+    return out
+
+
+def moving_fluid_costs(n=256, level=2, steps=10, warmup=3):
+    """Moving background fluid (mixed frame, App. B), 256^3 x 162 periodic,
+    the seeded shear flow: step time with FP32 and with FP16 populations."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    mf = W.moving_fluid(n)
+    fields = {k: torch.from_numpy(mf[k]).cuda() for k in ("v", "kt_a", "kt_0", "eta_t")}
+    E0 = torch.ones((n, n, n), dtype=torch.float32, device="cuda")
+    out = {}
+    for name, st in (("fp32", lbrt.LB_RT_F32), ("fp16", lbrt.LB_RT_F16_DEV)):
+        stream = torch.cuda.Stream()
+        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=level, cfl=CFL,
+                              moving=True, storage=st, stream=stream.cuda_stream)
+        lbrt.lb_rt_set_fluid(h, **fields)
+        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        lbrt.lb_rt_step(h, warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lbrt.lb_rt_step(h, steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "sd_s": n ** 3 * N / (ms * 1e-3)}
+        lbrt.lb_rt_destroy(h)
+        torch.cuda.empty_cache()
+    out["fp16_over_fp32"] = out["fp32"]["ms_per_step"] / out["fp16"]["ms_per_step"]
+    out["workload"] = "256^3 x 162 periodic shear flow (|v| <= 0.6), density-scaled opacities"
+    return out
+
+
 def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
     """Batched serving on the seeded request stream (sphere/shadow, n in
     {32..128}^3, 42 or 162 directions, kappa log-uniform 1e-1..1e4, 200-2000
@@ -259,6 +325,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-collision-modes", action="store_true")
+    ap.add_argument("--no-moving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -381,6 +449,16 @@ def main():
                 "ratio_vs_f32": ms_step / ms16,
                 "storage": "FP16 deviation from w_i E, float32 E per site, float32 arithmetic"},
     }
+    if not args.no_collision_modes and ws == 1:
+        try:
+            line["collision_modes"] = collision_mode_costs()
+        except Exception as e:  # report, do not hide
+            line["collision_modes"] = {"error": str(e)[:300]}
+    if not args.no_moving and ws == 1:
+        try:
+            line["moving_fluid"] = moving_fluid_costs()
+        except Exception as e:  # report, do not hide
+            line["moving_fluid"] = {"error": str(e)[:300]}
     if not args.no_serving and ws == 1:
         try:
             line["serving"] = serving_measurement()
