@@ -179,8 +179,10 @@ k_step_moving(const StepLaunch L, const MovingCoef cf, const DirTable t) {
       }
       const float beta = 1.f - fmaf(vx, nw.x, fmaf(vy, nw.y, vz * nw.z));
       const float Wb = W * beta;
-      const float A = 1.f / fmaf(dt * Wb, ksum, 1.f);
-      const float iWb = 1.f / Wb;
+      // fast reciprocals (a few ulp): the denominators are >= 1 and
+      // W beta >= W (1 - |v|) > 0
+      const float A = __fdividef(1.f, fmaf(dt * Wb, ksum, 1.f));
+      const float iWb = __fdividef(1.f, Wb);
       const float gg = A * dt * nw.w * (iWb * iWb * iWb);
       const float ai = A * r;
       const float b2 = beta * beta;
