@@ -650,11 +650,13 @@ cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const Di
 // tile loads zlen + 1 planes rounded up to whole batches, plus a small
 // per-tile overhead).
 cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage, int* nzc,
-                             int* ctas) {
+                             int* ctas, bool moving) {
   const int G = Ni / dpt;
   int per_sm = 0;
   cudaError_t e = cudaErrorInvalidValue;
-  if (storage == ST_F32) {
+  if (moving) {
+    e = occupancy_tma_moving(dpt, G, &per_sm);
+  } else if (storage == ST_F32) {
 #define LBRT_OCC(D, Z, T, B) \
   if (dpt == D && zc == Z) e = occupancy<false, D, Z, kRing, T, B>(G, &per_sm);
     LBRT_TILE_PLANS(LBRT_OCC)

@@ -95,7 +95,8 @@ void plan_directions(lb_rt* h) {
   const int N = h->N;
   h->ext_of_int.clear();
   h->int_of_ext.assign(N, -1);
-  if (h->cfg.moving) {
+  if (h->cfg.moving && h->cfg.storage != LB_RT_F32) {
+    // 16-bit moving fluid: the one-thread-per-site kernel, external order
     for (int e = 0; e < N; ++e) h->ext_of_int.push_back(e);
     h->dpt = h->zc = 0;
   } else {
@@ -110,9 +111,12 @@ void plan_directions(lb_rt* h) {
       });
     // the first plan (in the kernel's order of preference) that fits and
     // pads the direction set by at most 4 % more than the tightest plan
+    // (a moving fluid with no fitting plan falls back to the one-thread-per-
+    // site kernel with this ordering and no padding)
     const bool f32 = h->cfg.storage == LB_RT_F32;
-    const int (*plans)[3] = f32 ? kTilePlans : kTilePlans16;
-    const int nplans = f32 ? kNumTilePlans : kNumTilePlans16;
+    const bool mov = h->cfg.moving != 0;
+    const int (*plans)[3] = mov ? kTilePlansMoving : f32 ? kTilePlans : kTilePlans16;
+    const int nplans = mov ? kNumTilePlansMoving : f32 ? kNumTilePlans : kNumTilePlans16;
     std::vector<int> ni_of(nplans, -1);
     int min_ni = 1 << 30;
     for (int p = 0; p < nplans; ++p) {
@@ -122,7 +126,8 @@ void plan_directions(lb_rt* h) {
       for (auto& c : cls) ni += (int)(c.size() + dpt - 1) / dpt * dpt;
       const int warps = ni / dpt;
       if (ni > kMaxInternalDirs || 32 * warps > plans[p][2]) continue;
-      const size_t smem = f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
+      const size_t smem = mov ? step_tile_smem_moving(dpt, warps)
+                          : f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
       if (smem > 226 * 1024) continue;
       ni_of[p] = ni;
       min_ni = std::min(min_ni, ni);
@@ -347,7 +352,8 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     lb_rt_destroy(h);
     return LB_RT_ECUDA;
   }
-  if (!cfg->moving) {
+  const bool tiled = !cfg->moving || (cfg->storage == LB_RT_F32 && h->dpt > 0);
+  if (tiled) {
     std::string terr;
     for (int b = 0; b < 2; ++b) {
       const bool ok =
@@ -363,7 +369,8 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
       }
     }
     h->tmap_ok = true;
-    e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, cfg->storage, &h->nzc, &h->ctas);
+    e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, cfg->storage, &h->nzc, &h->ctas,
+                         cfg->moving != 0);
     if (e != cudaSuccess) {
       g_create_msg = std::string("static kernel grid: ") + cudaGetErrorString(e);
       lb_rt_destroy(h);

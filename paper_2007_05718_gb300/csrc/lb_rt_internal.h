@@ -164,7 +164,15 @@ size_t step_tile_smem(int dpt, int zc, int warps);
 // z chunks and CTA count of the static kernel's persistent grid for this
 // grid and plan on the current device (occupancy query).
 cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage, int* nzc,
-                             int* ctas);
+                             int* ctas, bool moving = false);
+// Moving fluid, FP32 populations, TMA tiles (kernels_tma_moving.cu): one
+// plane per batch; plans (directions per warp, 1, thread cap).
+extern const int kTilePlansMoving[][3];
+extern const int kNumTilePlansMoving;
+size_t step_tile_smem_moving(int dpt, int warps);
+cudaError_t occupancy_tma_moving(int dpt, int G, int* per_sm);
+cudaError_t launch_tma_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
+                              cudaStream_t s, int* nblocks);
 // 16-bit storage (kernels_tma16.cu): f_i = I_i / w_i = E (1 + q_i) with E a
 // padded float32 [PZ][PY][PX] array and q_i stored in FP16 or BF16.
 size_t step_tile_smem16(int dpt, int zc, int warps);
