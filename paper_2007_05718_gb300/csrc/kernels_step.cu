@@ -257,7 +257,9 @@ cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const D
 cudaError_t launch_step_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks) {
   // FP32 with a tile plan: the TMA-fed kernel; otherwise one thread per site
-  if (storage == ST_F32 && L.dpt > 0) return launch_tma_moving(L, c, t, s, nblocks);
+  if (L.dpt > 0)
+    return storage == ST_F32 ? launch_tma_moving(L, c, t, s, nblocks)
+                             : launch_tma16_moving(L, c, t, storage, s, nblocks);
   const int N = L.N;
   const int G = (N + 47) / 48;
   if (G > 4 || N < 1) return cudaErrorInvalidValue;

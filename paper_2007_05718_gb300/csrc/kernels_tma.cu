@@ -655,7 +655,8 @@ cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage
   int per_sm = 0;
   cudaError_t e = cudaErrorInvalidValue;
   if (moving) {
-    e = occupancy_tma_moving(dpt, G, &per_sm);
+    e = storage == ST_F32 ? occupancy_tma_moving(dpt, G, &per_sm)
+                          : occupancy_tma16_moving(storage, dpt, G, &per_sm);
   } else if (storage == ST_F32) {
 #define LBRT_OCC(D, Z, T, B) \
   if (dpt == D && zc == Z) e = occupancy<false, D, Z, kRing, T, B>(G, &per_sm);

@@ -547,6 +547,435 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
   }
 }
 
+// Moving background fluid (App. B) with 16-bit storage: the tiled moving
+// step of kernels_tma_moving.cu written in f = I / w.  With g'_i = A_i dt
+// (W beta_i)^-3 (so g_i = w_i g'_i), the warps accumulate sum w f*,
+// X = sum w beta^2 (g' eta_t + A f*), Y = sum w beta^2 g', sum w A f* and
+// sum w g'; the units form src = eta_t + kt_0 J and E' = sum w A f* + src
+// sum w g', store E^' and hand (src, 1/E^') to the output, which encodes
+// q = (A f* + g' src) / E^' - 1.  One plane per batch.
+struct DirConstM16 {
+  float4 s0, s1, s2, s3;  // (a_x, a_y), (a_z', n_x), (n_y, n_z), (w, dt) pairs
+  int sh, inert, pad0, pad1;
+};
+
+template <class ST, bool PER, int DPT, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
+k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap emap,
+                const StepLaunch L, const MovingCoef mc, const DirTable t) {
+  using C2 = Conv<ST>;
+  using T2 = typename C2::T2;
+  constexpr int ZC = 1;
+  constexpr int SLOTB = slot_bytes16<DPT, ZC>();
+  constexpr int ESLOT = eslot_floats<ZC>();
+  static_assert(SLOTB >= 5 * 64 * 4, "the partial sums must fit in a consumed slot");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int G = blockDim.y;
+  const int lane = threadIdx.x, g = threadIdx.y;
+  const Grid& gr = L.g;
+  const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
+  unsigned char* ring = smem_raw;
+  float* ering = reinterpret_cast<float*>(ring + (size_t)G * R * SLOTB);
+  float* coef = ering + R * ESLOT;  // [2][64]: src, 1 / E^'
+  DirConstM16* dirs = reinterpret_cast<DirConstM16*>(coef + 2 * 64);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(dirs + G * DPT);
+  unsigned long long* ebar = mbar + G * R;
+  double* bsum = reinterpret_cast<double*>(ebar + R);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 4);
+
+  const int nxb = (nx + 63) / 64;
+  const int ntiles = nxb * ny * L.nzc;
+  const long long sites = gr.sites;
+  const float dt = L.dt;
+  ST* __restrict__ out = static_cast<ST*>(L.out);
+  float* __restrict__ eout = L.e_out;
+  const int i0 = g * DPT;
+  const int oct0 = __float_as_int(t.au[i0].w);
+  const bool yneg = oct0 & 2;
+  const int zs = (oct0 & 4) ? 1 : 0;
+  const int row_own = yneg ? 0 : 1, row_up = yneg ? 1 : 0;
+  const int erow_up = yneg ? 2 : 0;
+  constexpr int nunits = 2;
+
+  for (int i = g * 32 + lane; i < G * DPT; i += G * 32) {
+    const float4 au = t.au[i], nw = t.nw[i];
+    const int oct = __float_as_int(au.w);
+    const float azw = (oct & 4) ? 1.f - au.z : au.z;
+    DirConstM16 d;
+    d.s0 = make_float4(au.x, au.x, au.y, au.y);
+    d.s1 = make_float4(azw, azw, nw.x, nw.x);
+    d.s2 = make_float4(nw.y, nw.y, nw.z, nw.z);
+    d.s3 = make_float4(nw.w, nw.w, dt, dt);
+    d.sh = (oct & 1) ? 1 : -1;
+    d.inert = oct & 8;
+    d.pad0 = d.pad1 = 0;
+    dirs[i] = d;
+  }
+  if (lane == 0) {
+    for (int r = 0; r < R; ++r) mbar_init(smem_u32(&mbar[g * R + r]), 1);
+    if (g == 0)
+      for (int r = 0; r < R; ++r) mbar_init(smem_u32(&ebar[r]), 1);
+  }
+  if (g == 0 && lane == 0) *abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  unsigned inert_mask = 0;
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) inert_mask |= dirs[i0 + k].inert ? 1u << k : 0u;
+
+  unsigned char* my_ring = ring + (size_t)g * R * SLOTB;
+  bool alive = true;
+  int issued = 0, waited = 0;
+  int is_t = blockIdx.x, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0, is_y = 0, is_zb = 0;
+  auto issue_seek = [&]() {
+    if (is_t < ntiles) {
+      const TileGeom tg = tile_geom(is_t, nxb, ny, nz, L.nzc);
+      is_M = tile_items<ZC>(tg.zlen);
+      is_x0 = tg.x0;
+      is_y = tg.y;
+      is_yp = yneg ? tg.y + 1 : tg.y;
+      is_zb = tg.zbeg;
+      is_zp = tg.zbeg + zs;
+    }
+  };
+  issue_seek();
+  auto issue = [&]() -> bool {
+    if (is_t >= ntiles || !alive) return false;
+    const int slot = issued % R;
+    __syncwarp();
+    if (lane == 0) {
+      const uint32_t bar = smem_u32(&mbar[g * R + slot]);
+      fence_proxy_async();
+      mbar_arrive_tx(bar, BOXH * DPT * 2 * ZC * 2);
+      tma_load_4d(smem_u32(my_ring + (size_t)slot * SLOTB), &tmap, is_x0, i0, is_yp,
+                  is_zp + is_m * ZC, bar);
+      if (g == 0) {
+        const uint32_t eb = smem_u32(&ebar[slot]);
+        mbar_arrive_tx(eb, BOXH * 3 * (ZC + 1) * 4);
+        tma_load_3d(smem_u32(ering + (size_t)slot * ESLOT), &emap, is_x0, is_y,
+                    is_zb + is_m * ZC, eb);
+      }
+    }
+    ++issued;
+    if (++is_m == is_M) {
+      is_m = 0;
+      is_t += gridDim.x;
+      issue_seek();
+    }
+    return true;
+  };
+  auto wait_item = [&](int q) -> bool {
+    if (!alive || *abort_flag) {
+      alive = false;
+      return false;
+    }
+    const uint32_t par = (uint32_t)((q / R) & 1);
+    if (!mbar_wait(smem_u32(&mbar[g * R + q % R]), par, L.err) ||
+        !mbar_wait(smem_u32(&ebar[q % R]), par, L.err)) {
+      *abort_flag = 1;
+      alive = false;
+      return false;
+    }
+    waited = q + 1;
+    return true;
+  };
+  const int wc = 2 + 2 * lane;
+  while (issued < R - 1 && issue()) {
+  }
+
+  float2 carry[DPT];
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) carry[k] = make_float2(0.f, 0.f);
+  float bud_a = 0.f, bud_b = 0.f;
+  double bud_da = 0.0, bud_db = 0.0;
+  const float2 one2 = make_float2(1.f, 1.f);
+  int q = 0;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const TileGeom tg = tile_geom(ti, nxb, ny, nz, L.nzc);
+    const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
+    const int M = tile_items<ZC>(tg.zlen);
+    const int xa = x0 + 2 * lane;
+    const bool in0 = xa < nx, in1 = xa + 1 < nx;
+    const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
+    const bool gx_hi = gr.periodic[0] && xa == 0;
+    const bool lo_from_y = xa + 1 == nx - 1;
+    const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
+    ST* const orow = out + (long long)i0 * gr.si + (long long)(y + 1) * gr.sy + xa + GL;
+    for (int m = 0; m < M; ++m, ++q) {
+      const int z = zbeg - 1 + m;
+      const bool zok = z >= zbeg && z < zend;
+      float2 vx, vy, vz, W, cA, et;
+      {
+        float a[2][6];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const bool v = zok && (xa + h < nx);
+          const long long st = v ? ((long long)z * ny + y) * nx + xa + h : 0;
+          a[h][0] = mc.v ? __ldg(mc.v + st) : 0.f;
+          a[h][1] = mc.v ? __ldg(mc.v + sites + st) : 0.f;
+          a[h][2] = mc.v ? __ldg(mc.v + 2 * sites + st) : 0.f;
+          a[h][3] = fld(mc.kta, mc.kta_s, st);
+          a[h][4] = fld(mc.kt0, mc.kt0_s, st);
+          a[h][5] = fld(mc.etat, mc.etat_s, st);
+        }
+        vx = make_float2(a[0][0], a[1][0]);
+        vy = make_float2(a[0][1], a[1][1]);
+        vz = make_float2(a[0][2], a[1][2]);
+        const float2 v2 = f2fma(vz, vz, f2fma(vy, vy, f2mul(vx, vx)));
+        W = make_float2(rsqrtf(1.f - v2.x), rsqrtf(1.f - v2.y));
+        cA = f2mul(f2mul(make_float2(dt, dt), W), make_float2(a[0][3] + a[0][4], a[1][3] + a[1][4]));
+        et = make_float2(a[0][5], a[1][5]);
+      }
+      // beta_i, A_i and g'_i = A_i dt (W beta_i)^-3 for direction constants d
+      auto coll = [&](const DirConstM16& d, float2& beta, float2& A, float2& gp) {
+        const float4 s1 = d.s1, s2 = d.s2, s3 = d.s3;
+        const float2 vn = f2fma(vz, make_float2(s2.z, s2.w),
+                                f2fma(vy, make_float2(s2.x, s2.y), f2mul(vx, make_float2(s1.z, s1.w))));
+        beta = f2sub(one2, vn);
+        const float2 den = f2fma(cA, beta, one2);
+        A = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));
+        const float2 wb = f2mul(W, beta);
+        const float2 iw = make_float2(__fdividef(1.f, wb.x), __fdividef(1.f, wb.y));
+        gp = f2mul(f2mul(A, make_float2(s3.z, s3.w)), f2mul(iw, f2mul(iw, iw)));
+      };
+      while (issued < q + R && issue()) {
+      }
+      wait_item(q);
+      unsigned char* slot = my_ring + (size_t)(q % R) * SLOTB;
+      const ST* sl = reinterpret_cast<const ST*>(slot);
+      const float* es = ering + (size_t)(q % R) * ESLOT;
+      const float* eo = es + (zs * 3 + 1) * BOXH + wc;
+      const float* eu = es + (zs * 3 + erow_up) * BOXH + wc;
+      const float2 EPo = *reinterpret_cast<const float2*>(eo);
+      const float2 EPu = *reinterpret_cast<const float2*>(eu);
+      const float Emo = eo[-1], Epo = eo[2], Emu = eu[-1], Epu = eu[2];
+      float2 Is[DPT];  // f*_i
+      float2 aS = make_float2(0.f, 0.f), aX = aS, aY = aS, aA = aS, aG = aS;
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) {
+        const DirConstM16& d = dirs[i0 + k];
+        const float4 s0 = d.s0, s1 = d.s1, s3 = d.s3;
+        const float2 ax = make_float2(s0.x, s0.y), ay = make_float2(s0.z, s0.w);
+        const float2 az = make_float2(s1.x, s1.y), w2 = make_float2(s3.x, s3.y);
+        const ST* po = sl + (row_own * DPT + k) * BOXH + wc;
+        const ST* pu = sl + (row_up * DPT + k) * BOXH + wc;
+        const float2 qo = C2::to2(*reinterpret_cast<const T2*>(po));
+        const float2 qu = C2::to2(*reinterpret_cast<const T2*>(pu));
+        const float2 fo = f2fma(EPo, qo, EPo);
+        const float2 fu = f2fma(EPu, qu, EPu);
+        float2 So, Su;
+        if (d.sh > 0) {
+          So = make_float2(fo.y, fmaf(Epo, C2::to1(po[2]), Epo));
+          Su = make_float2(fu.y, fmaf(Epu, C2::to1(pu[2]), Epu));
+        } else {
+          So = make_float2(fmaf(Emo, C2::to1(po[-1]), Emo), fo.x);
+          Su = make_float2(fmaf(Emu, C2::to1(pu[-1]), Emu), fu.x);
+        }
+        const float2 X0 = f2fma(ax, f2sub(So, fo), fo);
+        const float2 X1 = f2fma(ax, f2sub(Su, fu), fu);
+        const float2 Bn = f2fma(ay, f2sub(X1, X0), X0);
+        const float2 r = f2fma(az, f2sub(carry[k], Bn), Bn);
+        carry[k] = Bn;
+        Is[k] = r;
+        float2 beta, A, gp;
+        coll(d, beta, A, gp);
+        const float2 af = f2mul(A, r);
+        const float2 wb2 = f2mul(w2, f2mul(beta, beta));
+        aS = f2fma(w2, r, aS);
+        aX = f2fma(wb2, f2fma(gp, et, af), aX);
+        aY = f2fma(wb2, gp, aY);
+        aA = f2fma(w2, af, aA);
+        aG = f2fma(w2, gp, aG);
+      }
+      __syncwarp();
+      {
+        float2* p = reinterpret_cast<float2*>(slot) + lane;
+        p[0] = aS;
+        p[32] = aX;
+        p[64] = aY;
+        p[96] = aA;
+        p[128] = aG;
+      }
+      __syncthreads();
+      for (int u = g; u < nunits; u += G) {
+        const int f = (u << 5) + lane;
+        const int x = x0 + f;
+        const bool v = zok && x < nx;
+        const long long st = v ? ((long long)z * ny + y) * nx + x : 0;
+        const float ux = mc.v ? __ldg(mc.v + st) : 0.f;
+        const float uy = mc.v ? __ldg(mc.v + sites + st) : 0.f;
+        const float uz = mc.v ? __ldg(mc.v + 2 * sites + st) : 0.f;
+        const float kt0 = fld(mc.kt0, mc.kt0_s, st), etat = fld(mc.etat, mc.etat_s, st);
+        const int s = q % R;
+        float S = 0.f, X = 0.f, Y = 0.f, SA = 0.f, SG = 0.f;
+        for (int qq = 0; qq < G; ++qq) {
+          const float* p = reinterpret_cast<const float*>(ring + ((size_t)qq * R + s) * SLOTB) + f;
+          S += p[0];
+          X += p[64];
+          Y += p[128];
+          SA += p[192];
+          SG += p[256];
+        }
+        const float W2 = __fdividef(1.f, 1.f - fmaf(uz, uz, fmaf(uy, uy, ux * ux)));
+        const float J = __fdividef(W2 * X, 1.f - kt0 * W2 * Y);
+        const float src = fmaf(kt0, J, etat);
+        const float Enew = fmaf(SG, src, SA);
+        const float Eh = fmaxf(Enew, EPS_E);
+        coef[f] = src;
+        coef[64 + f] = __fdividef(1.f, Eh);
+        if (v) {
+          bud_a += S;
+          bud_b += Enew;
+          if (alive) store_e(eout, gr, z, y, x, Eh);
+        }
+      }
+      __syncthreads();
+      if (L.budget_partials && g < nunits) {
+        bud_da += (double)bud_a;
+        bud_db += (double)bud_b;
+        bud_a = bud_b = 0.f;
+      }
+      const float2 src = reinterpret_cast<const float2*>(coef)[lane];
+      const float2 rinv = reinterpret_cast<const float2*>(coef + 64)[lane];
+      const bool zface = gr.periodic[2] && (z == 0 || z == nz - 1);
+      const bool fast = __all_sync(0xffffffffu, in0 && in1) && zok &&
+                        !(y_face && ny == 1) && !(zface && nz == 1);
+      const bool xghost = __any_sync(0xffffffffu, gx_lo || gx_hi);
+      const int yface_rows = (y == ny - 1 ? 0 : ny + 1) - (y + 1);
+      if (alive && fast) {
+        ST* base = orow + (long long)(z + 1) * gr.sz;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          if (inert_mask >> k & 1u) continue;
+          float2 beta, A, gp;
+          coll(dirs[i0 + k], beta, A, gp);
+          const float2 qn = f2fma(f2fma(gp, src, f2mul(A, Is[k])), rinv, make_float2(-1.f, -1.f));
+          const T2 hq = C2::from2(qn);
+          ST* dst = base + (long long)k * gr.si;
+          if constexpr (!PER) {
+            *reinterpret_cast<T2*>(dst) = hq;
+          } else {
+            auto put = [&](ST* dd) {
+              *reinterpret_cast<T2*>(dd) = hq;
+              if (xghost) {
+                if (gx_lo) dd[GL - 1 - (xa + GL)] = lo_from_y ? hq.y : hq.x;
+                if (gx_hi) dd[nx + GL - (xa + GL)] = hq.x;
+              }
+            };
+            put(dst);
+            if (y_face) put(dst + (long long)yface_rows * gr.sy);
+            if (zface) {
+              const long long zd = (long long)((z == nz - 1 ? 0 : nz + 1) - (z + 1)) * gr.sz;
+              put(dst + zd);
+              if (y_face) put(dst + zd + (long long)yface_rows * gr.sy);
+            }
+          }
+        }
+      } else if (alive && in0 && zok) {
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          if (inert_mask >> k & 1u) continue;
+          float2 beta, A, gp;
+          coll(dirs[i0 + k], beta, A, gp);
+          const float2 qn = f2fma(f2fma(gp, src, f2mul(A, Is[k])), rinv, make_float2(-1.f, -1.f));
+          const T2 hq = C2::from2(qn);
+          store_pop(out, gr, i0 + k, z, y, xa, hq.x);
+          if (in1) store_pop(out, gr, i0 + k, z, y, xa + 1, hq.y);
+        }
+      }
+    }
+  }
+  for (int qq = waited; qq < issued; ++qq) {
+    const uint32_t par = (uint32_t)((qq / R) & 1);
+    mbar_wait(smem_u32(&mbar[g * R + qq % R]), par, L.err);
+    if (g == 0) mbar_wait(smem_u32(&ebar[qq % R]), par, L.err);
+  }
+  if (L.budget_partials) {
+    for (int s = 16; s > 0; s >>= 1) {
+      bud_da += __shfl_xor_sync(0xffffffffu, bud_da, s);
+      bud_db += __shfl_xor_sync(0xffffffffu, bud_db, s);
+    }
+    if (lane == 0 && g < nunits) {
+      bsum[2 * g] = bud_da;
+      bsum[2 * g + 1] = bud_db;
+    }
+    __syncthreads();
+    if (g == 0 && lane == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < min(G, nunits); ++w) {
+        a += bsum[2 * w];
+        b += bsum[2 * w + 1];
+      }
+      atomicAdd(L.budget_partials + 2 * blockIdx.x, a);
+      atomicAdd(L.budget_partials + 2 * blockIdx.x + 1, b);
+    }
+  }
+}
+
+template <int DPT, int R>
+size_t smem_moving16(int G) {
+  return (size_t)G * R * slot_bytes16<DPT, 1>() +
+         sizeof(float) * ((size_t)R * eslot_floats<1>() + 2 * 64) +
+         sizeof(DirConstM16) * (size_t)G * DPT + 8 * ((size_t)G * R + R) + sizeof(double) * 4 + 16;
+}
+
+template <class ST, bool PER, int DPT, int R, int MAXT, int REGS>
+cudaError_t set_attr_moving16() {
+  static unsigned long long attr_set = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_step_moving16<ST, PER, DPT, R, MAXT, REGS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024 - 1024);
+  if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
+  return e;
+}
+
+template <class ST, int DPT, int R, int MAXT, int REGS>
+cudaError_t occupancy_moving16_t(int G, int* per_sm) {
+  int a = 0, b = 0;
+  cudaError_t e = set_attr_moving16<ST, false, DPT, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_attr_moving16<ST, true, DPT, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_moving16<ST, false, DPT, R, MAXT, REGS>, 32 * G, smem_moving16<DPT, R>(G));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_moving16<ST, true, DPT, R, MAXT, REGS>, 32 * G, smem_moving16<DPT, R>(G));
+  *per_sm = std::min(a, b);
+  return e;
+}
+
+template <class ST, int DPT, int R, int MAXT, int REGS>
+cudaError_t launch_moving16_t(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
+                              cudaStream_t s, int* nblocks) {
+  const int G = L.N / DPT;
+  if (!L.tmap_in || !L.tmap_e || !L.e_out || G < 1 || G * DPT != L.N || 32 * G > MAXT ||
+      L.nzc < 1 || L.nzc > L.g.nz || L.ctas < 1)
+    return cudaErrorInvalidValue;
+  if (L.budget_partials && L.ctas > L.partials_cap) return cudaErrorInvalidValue;
+  if (nblocks) *nblocks = L.ctas;
+  const size_t smem = smem_moving16<DPT, R>(G);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const bool per = L.g.periodic[0] || L.g.periodic[1] || L.g.periodic[2];
+  const cudaError_t e = per ? set_attr_moving16<ST, true, DPT, R, MAXT, REGS>()
+                            : set_attr_moving16<ST, false, DPT, R, MAXT, REGS>();
+  if (e != cudaSuccess) return e;
+  if (per)
+    k_step_moving16<ST, true, DPT, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, *L.tmap_e, L, c, t);
+  else
+    k_step_moving16<ST, false, DPT, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, *L.tmap_e, L, c, t);
+  return cudaGetLastError();
+}
+
+#define LBRT_MOVING16_PLANS(X) \
+  X(5, 320, 96)                \
+  X(11, 512, 128)              \
+  X(10, 544, 96)
+
 template <int DPT, int ZC, int R>
 size_t step_smem16(int G) {
   return (size_t)G * R * slot_bytes16<DPT, ZC>() + sizeof(float) * ((size_t)R * eslot_floats<ZC>() + ZC * 5 * 64) +
@@ -709,6 +1138,28 @@ cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const 
 cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch) {
   if (storage == ST_F16) return occupancy_typed<__half>(dpt, zc, G, per_sm, batch);
   if (storage == ST_BF16) return occupancy_typed<__nv_bfloat16>(dpt, zc, G, per_sm, batch);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_tma16_moving(int storage, int dpt, int G, int* per_sm) {
+#define LBRT_M16O(D, T, B)                                                                    \
+  if (dpt == D)                                                                             \
+    return storage == ST_BF16 ? occupancy_moving16_t<__nv_bfloat16, D, kRing16, T, B>(G, per_sm) \
+                              : occupancy_moving16_t<__half, D, kRing16, T, B>(G, per_sm);
+  LBRT_MOVING16_PLANS(LBRT_M16O)
+#undef LBRT_M16O
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tma16_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
+                                int storage, cudaStream_t s, int* nblocks) {
+#define LBRT_M16L(D, T, B)                                                            \
+  if (L.dpt == D && L.zc == 1)                                                        \
+    return storage == ST_BF16                                                         \
+               ? launch_moving16_t<__nv_bfloat16, D, kRing16, T, B>(L, c, t, s, nblocks) \
+               : launch_moving16_t<__half, D, kRing16, T, B>(L, c, t, s, nblocks);
+  LBRT_MOVING16_PLANS(LBRT_M16L)
+#undef LBRT_M16L
   return cudaErrorInvalidValue;
 }
 

@@ -95,11 +95,7 @@ void plan_directions(lb_rt* h) {
   const int N = h->N;
   h->ext_of_int.clear();
   h->int_of_ext.assign(N, -1);
-  if (h->cfg.moving && h->cfg.storage != LB_RT_F32) {
-    // 16-bit moving fluid: the one-thread-per-site kernel, external order
-    for (int e = 0; e < N; ++e) h->ext_of_int.push_back(e);
-    h->dpt = h->zc = 0;
-  } else {
+  {
     std::vector<std::vector<int>> cls(4);
     for (int e = 0; e < N; ++e) {
       const int c = (h->n[3 * e + 1] < 0 ? 1 : 0) | (h->n[3 * e + 2] < 0 ? 2 : 0);
@@ -352,7 +348,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     lb_rt_destroy(h);
     return LB_RT_ECUDA;
   }
-  const bool tiled = !cfg->moving || (cfg->storage == LB_RT_F32 && h->dpt > 0);
+  const bool tiled = !cfg->moving || h->dpt > 0;
   if (tiled) {
     std::string terr;
     for (int b = 0; b < 2; ++b) {

@@ -173,6 +173,9 @@ size_t step_tile_smem_moving(int dpt, int warps);
 cudaError_t occupancy_tma_moving(int dpt, int G, int* per_sm);
 cudaError_t launch_tma_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                               cudaStream_t s, int* nblocks);
+cudaError_t occupancy_tma16_moving(int storage, int dpt, int G, int* per_sm);
+cudaError_t launch_tma16_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
+                                int storage, cudaStream_t s, int* nblocks);
 // 16-bit storage (kernels_tma16.cu): f_i = I_i / w_i = E (1 + q_i) with E a
 // padded float32 [PZ][PY][PX] array and q_i stored in FP16 or BF16.
 size_t step_tile_smem16(int dpt, int zc, int warps);
