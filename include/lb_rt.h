@@ -164,6 +164,16 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps);
 lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P,
                            lb_rt_budget* budget, int ptr_kind);
 
+/* Coupling outputs of the current state for a fluid code (Sec. 4, step 4 of
+ * the coupling): the comoving radiation energy density J [sites] and
+ * momentum density H [3][sites] (Eq. J), and the radiative four-force
+ * S [4][sites] = (S_0, S_x, S_y, S_z) with S_0 = W (kt_a J - eta_t) + kt H_0,
+ * S_j = W (kt_a J - eta_t) v_j + kt H_j, kt = kt_a + kt_0, H_0 = -v.H (from
+ * H_mu u^mu = 0, signature -+++).  A static handle uses v = 0 and its static
+ * opacities.  Any output may be NULL.  With host pointers the call
+ * synchronises the stream.  Errors: EINVAL, ECUDA. */
+lb_rt_status lb_rt_coupling(lb_rt* h, float* J, float* H, float* S, int ptr_kind);
+
 /* Decoded float32 populations, direction-major [N][sites]. */
 lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind);
 

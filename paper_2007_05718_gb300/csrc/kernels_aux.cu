@@ -3,6 +3,7 @@
 // float32, frozen-cell overwrite and the FP64 energy-budget reductions.
 // Every population write also writes the site's periodic ghost mirrors.
 #include <algorithm>
+#include <type_traits>
 
 #include "lb_rt_internal.h"
 
@@ -378,6 +379,77 @@ __global__ void k_total_partials16(Grid g, int N, const ST* __restrict__ pop,
   if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
+// Coupling outputs (Sec. 4, coupling step 4): from the site's E, F, P and
+// the fluid velocity v, the comoving J = W^2 (E - 2 F.v + P:vv) (Eq. J),
+// H_j = W^3 (F.v - E) v_j + W h_ji F^i - W h_ji v_k P^ik with
+// h_ij = W^2 v_i v_j + delta_ij, H_0 = -v.H (from H_mu u^mu = 0, signature
+// -+++), and S_0 = W (kt_a J - eta_t) + kt H_0, S_j = W (kt_a J - eta_t) v_j +
+// kt H_j with kt = kt_a + kt_0 (kt_1 = 0).  ST = float: populations; 16-bit
+// types: the deviation form against the E array `e`.
+template <class ST>
+__global__ void k_coupling(Grid g, int N, const ST* __restrict__ pop, const float* __restrict__ e,
+                           DirTable t, MovingCoef c, float* __restrict__ Jo, float* __restrict__ Ho,
+                           float* __restrict__ So) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.sites) return;
+  int x, y, z;
+  site_xyz(g, s, x, y, z);
+  float Eh = 0.f;
+  if (!std::is_same<ST, float>::value) Eh = e[eidx(g, z, y, x)];
+  float E = 0, Fx = 0, Fy = 0, Fz = 0, Pxx = 0, Pxy = 0, Pxz = 0, Pyy = 0, Pyz = 0, Pzz = 0;
+  for (int i = 0; i < N; ++i) {
+    const float4 nw = t.nw[i];
+    float I;
+    if constexpr (std::is_same<ST, float>::value) I = pop[pidx(g, i, z, y, x)];
+    else I = nw.w * fmaf(Eh, to_f<ST>(pop[pidx(g, i, z, y, x)]), Eh);
+    E += I;
+    Fx = fmaf(nw.x, I, Fx);
+    Fy = fmaf(nw.y, I, Fy);
+    Fz = fmaf(nw.z, I, Fz);
+    Pxx = fmaf(nw.x * nw.x, I, Pxx);
+    Pxy = fmaf(nw.x * nw.y, I, Pxy);
+    Pxz = fmaf(nw.x * nw.z, I, Pxz);
+    Pyy = fmaf(nw.y * nw.y, I, Pyy);
+    Pyz = fmaf(nw.y * nw.z, I, Pyz);
+    Pzz = fmaf(nw.z * nw.z, I, Pzz);
+  }
+  const float vx = c.v ? c.v[s] : 0.f, vy = c.v ? c.v[g.sites + s] : 0.f,
+              vz = c.v ? c.v[2 * g.sites + s] : 0.f;
+  const float W2 = 1.f / (1.f - (vx * vx + vy * vy + vz * vz));
+  const float W = sqrtf(W2);
+  const float Fv = Fx * vx + Fy * vy + Fz * vz;
+  // Pv_i = P^ik v_k
+  const float Pvx = Pxx * vx + Pxy * vy + Pxz * vz;
+  const float Pvy = Pxy * vx + Pyy * vy + Pyz * vz;
+  const float Pvz = Pxz * vx + Pyz * vy + Pzz * vz;
+  const float Pvv = Pvx * vx + Pvy * vy + Pvz * vz;
+  const float J = W2 * (E - 2.f * Fv + Pvv);
+  // h_ji a^i = a_j + W^2 v_j (v.a) for a = F - Pv
+  const float ax = Fx - Pvx, ay = Fy - Pvy, az = Fz - Pvz;
+  const float va = vx * ax + vy * ay + vz * az;
+  const float c1 = W * W2 * (Fv - E), c2 = W * W2 * va;
+  const float Hx = c1 * vx + W * ax + c2 * vx;
+  const float Hy = c1 * vy + W * ay + c2 * vy;
+  const float Hz = c1 * vz + W * az + c2 * vz;
+  if (Jo) Jo[s] = J;
+  if (Ho) {
+    Ho[s] = Hx;
+    Ho[g.sites + s] = Hy;
+    Ho[2 * g.sites + s] = Hz;
+  }
+  if (So) {
+    const float kta = c.kta ? c.kta[s] : c.kta_s, kt0 = c.kt0 ? c.kt0[s] : c.kt0_s;
+    const float etat = c.etat ? c.etat[s] : c.etat_s;
+    const float kt = kta + kt0;
+    const float H0 = -(vx * Hx + vy * Hy + vz * Hz);
+    const float emit = W * (kta * J - etat);
+    So[s] = fmaf(kt, H0, emit);
+    So[g.sites + s] = fmaf(kt, Hx, emit * vx);
+    So[2 * g.sites + s] = fmaf(kt, Hy, emit * vy);
+    So[3 * g.sites + s] = fmaf(kt, Hz, emit * vz);
+  }
+}
+
 unsigned grid1d(long long n) { return (unsigned)((n + BLK - 1) / BLK); }
 
 }  // namespace
@@ -439,6 +511,21 @@ cudaError_t launch_frozen(const Grid& g, int Ni, int Next, const int* int_of_ext
     k_frozen16<__nv_bfloat16><<<nb, BLK, 0, s>>>(g, Ni, Next, int_of_ext, ncells, cells, vals,
                                                  static_cast<__nv_bfloat16*>(pop), e,
                                                  injection_acc, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coupling(const Grid& g, int N, const void* pop, const float* e, int storage,
+                            const DirTable& t, const MovingCoef& c, float* J, float* H, float* S,
+                            cudaStream_t s) {
+  if (storage == ST_F32)
+    k_coupling<float><<<grid1d(g.sites), BLK, 0, s>>>(g, N, static_cast<const float*>(pop), e, t,
+                                                      c, J, H, S);
+  else if (storage == ST_F16)
+    k_coupling<__half><<<grid1d(g.sites), BLK, 0, s>>>(g, N, static_cast<const __half*>(pop), e,
+                                                       t, c, J, H, S);
+  else
+    k_coupling<__nv_bfloat16><<<grid1d(g.sites), BLK, 0, s>>>(
+        g, N, static_cast<const __nv_bfloat16*>(pop), e, t, c, J, H, S);
   return cudaGetLastError();
 }
 

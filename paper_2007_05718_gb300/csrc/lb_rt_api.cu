@@ -602,6 +602,36 @@ lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P, lb_rt_budget*
   return LB_RT_OK;
 }
 
+lb_rt_status lb_rt_coupling(lb_rt* h, float* J, float* H, float* S, int ptr_kind) {
+  if (!h) return LB_RT_EINVAL;
+  if (ptr_kind != LB_RT_HOST && ptr_kind != LB_RT_DEVICE)
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
+  if (!J && !H && !S) return LB_RT_OK;
+  const long long S_ = h->grid.sites;
+  // a static fluid is the moving one at rest with its own opacities
+  MovingCoef c = h->mc;
+  if (!h->cfg.moving) {
+    c = MovingCoef{nullptr, h->sc.ka, h->sc.k0, h->sc.eta, h->sc.ka_s, h->sc.k0_s, h->sc.eta_s};
+  }
+  float *dJ = J, *dH = H, *dS = S;
+  if (ptr_kind == LB_RT_HOST) {
+    if (!h->scratch) CK(h, cudaMalloc((void**)&h->scratch, sizeof(float) * 10 * S_));
+    dJ = J ? h->scratch : nullptr;
+    dH = H ? h->scratch + S_ : nullptr;
+    dS = S ? h->scratch + 4 * S_ : nullptr;
+  }
+  cudaError_t e = launch_coupling(h->grid, h->Ni, h->pop[h->cur], h->ef[h->cur], h->cfg.storage,
+                                  h->table, c, dJ, dH, dS, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "coupling kernel");
+  if (ptr_kind == LB_RT_HOST) {
+    if (J) CK(h, cudaMemcpyAsync(J, dJ, sizeof(float) * S_, cudaMemcpyDeviceToHost, h->stream));
+    if (H) CK(h, cudaMemcpyAsync(H, dH, sizeof(float) * 3 * S_, cudaMemcpyDeviceToHost, h->stream));
+    if (S) CK(h, cudaMemcpyAsync(S, dS, sizeof(float) * 4 * S_, cudaMemcpyDeviceToHost, h->stream));
+    return lb_rt_sync(h);
+  }
+  return LB_RT_OK;
+}
+
 lb_rt_status lb_rt_get_populations(lb_rt* h, float* out, int ptr_kind) {
   if (!h || !out) return fail(h, LB_RT_EINVAL, "null argument");
   const size_t count = (size_t)h->grid.sites * h->N;

@@ -149,6 +149,10 @@ cudaError_t launch_frozen(const Grid& g, int Ni, int Next, const int* int_of_ext
                           int storage, const DirTable& t, double* injection_acc, cudaStream_t s);
 cudaError_t launch_budget_finalize(const double* partials, int nblocks, double* acc,
                                    cudaStream_t s);
+// Coupling outputs J [sites], H [3][sites], S [4][sites] (any may be null).
+cudaError_t launch_coupling(const Grid& g, int N, const void* pop, const float* e, int storage,
+                            const DirTable& t, const MovingCoef& c, float* J, float* H, float* S,
+                            cudaStream_t s);
 cudaError_t launch_total_energy(const Grid& g, int N, const void* pop, const float* e, int storage,
                                 const DirTable& t, double* partials, int max_blocks, double* out,
                                 cudaStream_t s);

@@ -30,7 +30,7 @@ EXPORTED = [
     "lb_rt_moments", "lb_rt_get_populations", "lb_rt_state_bytes", "lb_rt_save_state",
     "lb_rt_restore_state", "lb_rt_sync", "lb_rt_directions", "lb_rt_enable_timing",
     "lb_rt_last_step_ms", "lb_rt_last_error", "lb_rt_version", "lb_rt_destroy",
-    "lb_rt_total_energy_noalloc",
+    "lb_rt_total_energy_noalloc", "lb_rt_coupling",
     "lb_rt_batch_create", "lb_rt_batch_destroy", "lb_rt_batch_problem_bytes", "lb_rt_batch_admit",
     "lb_rt_batch_tick", "lb_rt_batch_sync", "lb_rt_batch_poll", "lb_rt_batch_moments",
     "lb_rt_batch_steps", "lb_rt_batch_release", "lb_rt_batch_tuning", "lb_rt_batch_last_error",
@@ -114,6 +114,7 @@ def load(path=LIB_PATH):
         "lb_rt_destroy": (None, [H]),
         "lb_rt_total_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
                                                  C.c_int, C.c_void_p]),
+        "lb_rt_coupling": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
         "lb_rt_batch_create": (C.c_int, [C.POINTER(lb_rt_batch_config), C.POINTER(C.c_void_p)]),
         "lb_rt_batch_destroy": (None, [H]),
         "lb_rt_batch_problem_bytes": (C.c_size_t, [H, C.POINTER(lb_rt_config)]),
@@ -303,6 +304,12 @@ def lb_rt_moments(h, E=None, F=None, P=None, budget=False):
     _check(h, load().lb_rt_moments(h, _ptr(E)[0], _ptr(F)[0], _ptr(P)[0],
                                    C.byref(b) if budget else None, kind))
     return b.as_dict() if budget else None
+
+
+def lb_rt_coupling(h, J=None, H=None, S=None):
+    """Comoving J [sites], H [3, sites] and the four-force S [4, sites]."""
+    kind = _kind_of([J, H, S])
+    _check(h, load().lb_rt_coupling(h, _ptr(J)[0], _ptr(H)[0], _ptr(S)[0], kind))
 
 
 def lb_rt_get_populations(h, out):
