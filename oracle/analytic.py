@@ -109,3 +109,36 @@ def dense_moving_solve(Is, n, w, dt, v, kt_a, kt_0, eta_t):
     M = np.diag(1.0 + dt * W * beta * (kt_a + kt_0))
     M -= dt * kt_0 * W ** 2 * (w * D)[:, None] * (beta ** 2)[None, :]
     return np.linalg.solve(M, Is + dt * w * D * eta_t)
+
+
+def wave_shell_E(r, t, R):
+    """Free streaming of a uniform isotropic ball (radius R, E = 1) in vacuum:
+    E(r, t) is the fraction of directions n with |r - n t| < R, i.e.
+    (1 - c*) / 2 with c* = (r^2 + t^2 - R^2) / (2 r t), clipped to [0, 1]
+    (c* <= -1 inside the moving ball).  Any direction set gives this shell
+    average, since every direction carries a translated copy of the ball."""
+    r = np.asarray(r, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = (r ** 2 + t ** 2 - R ** 2) / (2.0 * r * t)
+    c = np.where(r * t > 0, c, np.where(r < R, -1.0, 1.0))
+    return np.clip((1.0 - np.clip(c, -1.0, 1.0)) / 2.0, 0.0, 1.0)
+
+
+def wave_peak(t, R):
+    """max_r wave_shell_E(r, t, R) = (1 - sqrt(1 - R^2 / t^2)) / 2 for t > R
+    (at r = sqrt(t^2 - R^2)); tends to R^2 / (4 t^2), the inverse-square law."""
+    return (1.0 - math.sqrt(1.0 - (R / t) ** 2)) / 2.0
+
+
+def wave_second_moment(lat, ball_mass, ball_S2, steps):
+    """Exact energy-weighted second moment sum_x E |x - c|^2 (cells^2) of the
+    discrete pull scheme after `steps` steps in vacuum, before any energy
+    leaves the box: each direction carries the ball shifted by a binomial
+    walk with success probability a = cfl |n^a| per axis (Eq. interp), so
+    sum_i w_i [S2 + m (steps^2 cfl^2 |n_i|^2 + steps sum_a a (1 - a))] with
+    m and S2 the ball's mass and second moment about its centre."""
+    a = lat.cfl * np.abs(lat.n[:, :lat.dims])
+    walk = steps ** 2 * lat.cfl ** 2 * np.sum(lat.n[:, :lat.dims] ** 2, axis=1) \
+        + steps * np.sum(a * (1.0 - a), axis=1)
+    return float(np.sum(lat.w * (ball_S2 + ball_mass * walk)))
+

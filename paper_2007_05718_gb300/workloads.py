@@ -71,6 +71,18 @@ def shadow(n, kappa_emit, R=0.125, emit_centre=(0.25, 0.5, 0.5),
             "E0": E0.astype(np.float32)}
 
 
+def wave_ball(n, R_cells, centre=None):
+    """Free-streaming wave (Sec. 4.1, radiation wave): E0 = 1 at cell centres
+    closer than R_cells cells to the centre of an n^3 box, 0 elsewhere
+    (isotropic populations I_i = w_i E0 are set by the caller).  Returns
+    (E0 float32 [n, n, n], centre in cell units)."""
+    c = (n / 2.0,) * 3 if centre is None else centre
+    idx = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    r2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2
+    return (r2 < R_cells ** 2).astype(np.float32), c
+
+
 def random_fields(shape, seed, lo=0.5, hi=1.5):
     """Strictly positive seeded field, uniform in [lo, hi)."""
     g = np.random.default_rng(seed)

@@ -114,3 +114,37 @@ def test_gaussian_diffusion_3d_implicit():
     assert np.linalg.norm(E - Ea) / np.linalg.norm(Ea) < crit
     E2 = A.gaussian_E(r2, t, 4 / L, Dc, dims=2)   # the 2D amplitude is wrong in 3D
     assert np.linalg.norm(E - E2) / np.linalg.norm(E2) > 2 * crit
+
+
+def test_free_streaming_wave_exact_moments():
+    """Radiation wave (Sec. 4.1) in vacuum: energy is conserved exactly and
+    the energy-weighted second moment grows exactly as the binomial walk of
+    each direction predicts; the shell-averaged profile follows the
+    direction-set independent closed form within the interpolation blur."""
+    from oracle import analytic as A
+    from oracle import directions as D
+    from oracle import lb
+    from paper_2007_05718_gb300 import workloads as W
+    n, R, steps = 48, 5.0, 16   # the walk reaches at most R + steps < n / 2: no outflow
+    E0, c = W.wave_ball(n, R)
+    nv, w = D.icosphere(1)
+    lat = lb.Lattice(3, (n, n, n), nv, w, cfl=0.2, dx=1.0, bc=(lb.VACUUM,) * 3)
+    I = lb.isotropic(E0.astype(float), lat)
+    idx = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    r2 = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2
+    m = float(E0.sum())
+    S2 = float((E0 * r2).sum())
+    I = lb.run(I, lat, lb.Static(), steps)
+    E = I.sum(axis=0)
+    assert abs(E.sum() - m) < 1e-12 * m
+    M2 = float((E * r2).sum())
+    assert abs(M2 - A.wave_second_moment(lat, m, S2, steps)) < 1e-10 * M2
+    # first moment stays at the centre (symmetric direction set)
+    assert abs(float((E * (X - c[0])).sum())) < 1e-9 * m
+    # the closed form's peak tends to the inverse-square law
+    assert abs(A.wave_peak(1000.0, 5.0) * 4 * 1000.0 ** 2 / 25.0 - 1.0) < 1e-4
+    # shell average of the closed form conserves the ball's energy
+    rr = np.linspace(0.01, 40, 20001)
+    tot = np.trapezoid(A.wave_shell_E(rr, 12.0, 5.0) * 4 * np.pi * rr ** 2, rr)
+    assert abs(tot / (4.0 / 3.0 * np.pi * 125.0) - 1.0) < 1e-3
