@@ -164,7 +164,7 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps);
 lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P,
                            lb_rt_budget* budget, int ptr_kind);
 
-/* Coupling outputs of the current state for a fluid code (Sec. 4, step 4 of
+/* Coupling outputs of the current state for a fluid code (Sec. 5, step 4 of
  * the coupling): the comoving radiation energy density J [sites] and
  * momentum density H [3][sites] (Eq. J), and the radiative four-force
  * S [4][sites] = (S_0, S_x, S_y, S_z) with S_0 = W (kt_a J - eta_t) + kt H_0,

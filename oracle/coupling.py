@@ -1,6 +1,6 @@
 """Coupling outputs of the radiation field for a fluid code, FP64 (oracle).
 
-Sec. 4 (coupling with a relativistic fluid code, step 4) gives, from the
+Sec. 5 (coupling with a relativistic fluid code, step 4) gives, from the
 lab-frame moments E, F^i, P^ij and the fluid three-velocity v (c = 1):
 
   J   = W^2 (E - 2 F.v + P:vv)                          (Eq. J, comoving energy density)

@@ -379,7 +379,7 @@ __global__ void k_total_partials16(Grid g, int N, const ST* __restrict__ pop,
   if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-// Coupling outputs (Sec. 4, coupling step 4): from the site's E, F, P and
+// Coupling outputs (Sec. 5, coupling step 4): from the site's E, F, P and
 // the fluid velocity v, the comoving J = W^2 (E - 2 F.v + P:vv) (Eq. J),
 // H_j = W^3 (F.v - E) v_j + W h_ji F^i - W h_ji v_k P^ik with
 // h_ij = W^2 v_i v_j + delta_ij, H_0 = -v.H (from H_mu u^mu = 0, signature

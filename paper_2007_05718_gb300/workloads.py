@@ -72,7 +72,7 @@ def shadow(n, kappa_emit, R=0.125, emit_centre=(0.25, 0.5, 0.5),
 
 
 def wave_ball(n, R_cells, centre=None):
-    """Free-streaming wave (Sec. 4.1, radiation wave): E0 = 1 at cell centres
+    """Free-streaming wave (Sec. 4.1.2, radiation wave): E0 = 1 at cell centres
     closer than R_cells cells to the centre of an n^3 box, 0 elsewhere
     (isotropic populations I_i = w_i E0 are set by the caller).  Returns
     (E0 float32 [n, n, n], centre in cell units)."""

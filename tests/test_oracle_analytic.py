@@ -117,7 +117,7 @@ def test_gaussian_diffusion_3d_implicit():
 
 
 def test_free_streaming_wave_exact_moments():
-    """Radiation wave (Sec. 4.1) in vacuum: energy is conserved exactly and
+    """Radiation wave (Sec. 4.1.2) in vacuum: energy is conserved exactly and
     the energy-weighted second moment grows exactly as the binomial walk of
     each direction predicts; the shell-averaged profile follows the
     direction-set independent closed form within the interpolation blur."""

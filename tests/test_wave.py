@@ -1,4 +1,4 @@
-"""Radiation wave in the free-streaming regime (Sec. 4.1): a uniform
+"""Radiation wave in the free-streaming regime (Sec. 4.1.2): a uniform
 isotropic ball streams outwards in vacuum.  Reduced-size parity against the
 oracle, and the paper's full-size case (200^3, CFL 0.2, ball of radius 16
 cells, 200 steps) checked against the exact discrete identities (energy,
