@@ -8,8 +8,9 @@ Prints one JSON line.  `value` is site-direction updates per second over
 the timed steps (inputs resident in HBM, 705 MB of populations per step,
 larger than L2); `e2e` is the same metric through the C ABI with host
 buffers: every step copies new fluid coefficients (kappa_a, eta) from pinned
-host memory, steps, and reads E and F back to the host, as a coupled
-hydrodynamics code does each step.
+host memory (lb_rt_set_fluid), steps, and returns E and F to pinned host
+memory (lb_rt_step_moments: the step kernel's collision epilogue writes them
+across the host link), as a coupled hydrodynamics code does each step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -403,8 +404,7 @@ def main():
         F_h = torch.empty((3, sites), dtype=torch.float32).pin_memory()
         for _ in range(2):
             lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
-            lbrt.lb_rt_step(h, 1)
-            lbrt.lb_rt_moments(h, E=E_h, F=F_h)
+            lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         torch.cuda.synchronize()
         _barrier(ws)
         te = time.perf_counter()
@@ -413,8 +413,7 @@ def main():
         e0.record(stream)
         for _ in range(args.e2e_steps):
             lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
-            lbrt.lb_rt_step(h, 1)
-            lbrt.lb_rt_moments(h, E=E_h, F=F_h)
+            lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         e1.record(stream)
         e1.synchronize()
         wall = time.perf_counter() - te
@@ -443,7 +442,9 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * sites,
-                "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps},
+                "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps,
+                "route": "lb_rt_set_fluid(kappa_a, eta from pinned host) + "
+                         "lb_rt_step_moments(1 step, E and F to pinned host)"},
         "clocks": ck,
         "f16": {"value": sd_step * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
                 "ratio_vs_f32": ms_step / ms16,

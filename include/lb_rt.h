@@ -164,6 +164,24 @@ lb_rt_status lb_rt_step(lb_rt* h, int nsteps);
 lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P,
                            lb_rt_budget* budget, int ptr_kind);
 
+/* lb_rt_step followed by the moments E [sites] and F [3][sites] of the new
+ * state (the coupling loop of Sec. 5: step 3 then step 4), with E and F taken
+ * from the last step's collision instead of a second pass over the
+ * populations.  The collision writes I' = alpha I* + w_i (c0 + n_i . c1)
+ * (Sec. 3.3, Eq. rte_implicit); for an isotropic table (Eq. iso-tensors:
+ * sum w = 1, sum w n = 0, sum w n n = Id/d) its moments are E' = alpha E* + c0
+ * and F' = alpha F* + c1/d, which the step kernel stores per site.
+ * Host pointers to page-locked memory that the device can address
+ * (cudaHostAlloc, cudaHostRegister) are written by the step kernel itself
+ * across the host link; other host memory goes through a device buffer.
+ * With host pointers the call synchronises the stream.  For 16-bit storage,
+ * a moving fluid, frozen cells, a table that is not isotropic, or nsteps = 0,
+ * it runs lb_rt_step and then lb_rt_moments.  E or F may be NULL.
+ * Agrees with lb_rt_step + lb_rt_moments to float32 rounding (the two sum in
+ * different orders).  Errors: EINVAL, ECUDA, ETIMEDOUT as lb_rt_step and
+ * lb_rt_sync. */
+lb_rt_status lb_rt_step_moments(lb_rt* h, int nsteps, float* E, float* F, int ptr_kind);
+
 /* Coupling outputs of the current state for a fluid code (Sec. 5, step 4 of
  * the coupling): the comoving radiation energy density J [sites] and
  * momentum density H [3][sites] (Eq. J), and the radiative four-force

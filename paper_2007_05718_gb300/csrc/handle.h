@@ -33,6 +33,7 @@ struct lb_rt {
   CUtensorMap tmap[2];                 // TMA descriptors of pop[0] / pop[1]
   CUtensorMap emap[2];                 // 16-bit storage: TMA descriptors of ef[0] / ef[1]
   bool tmap_ok = false;
+  bool iso = false;             // isotropic table: sum w = 1, sum w n = 0, sum w n n = Id / d
   int cur = 0;
   size_t pop_bytes = 0;
   // coefficient fields: static ka, k0, lam, eta (slots 0-3); moving v(3), kta, kt0, etat (4-7)

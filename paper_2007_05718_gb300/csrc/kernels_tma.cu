@@ -318,6 +318,16 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
         if (v) {
           bud_a += E;
           bud_b += cc.Enew;
+          // moments of I' = alpha I* + w (c0 + n . c1) for an isotropic table
+          // (sum w = 1, sum w n = 0, sum w n n = Id / d): E' = alpha E* + c0 =
+          // Enew, F' = alpha F* + c1 / d
+          if (!BATCH && one.mom_E) one.mom_E[((long long)z * ny + y) * nx + x] = cc.Enew;
+          if (!BATCH && one.mom_F) {
+            const long long st = ((long long)z * ny + y) * nx + x;
+            one.mom_F[st] = fmaf(cc.alpha, Fx, cc.c1x * inv_d);
+            one.mom_F[gr.sites + st] = fmaf(cc.alpha, Fy, cc.c1y * inv_d);
+            one.mom_F[2 * gr.sites + st] = fmaf(cc.alpha, Fz, cc.c1z * inv_d);
+          }
         }
       }
       __syncthreads();
@@ -553,6 +563,8 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   one.tile_start = 0;
   one.ntiles = (L.g.nx + 63) / 64 * L.g.ny * L.nzc;
   one.budget_partials = L.budget_partials;
+  one.mom_E = L.mom_E;
+  one.mom_F = L.mom_F;
   if (per)
     k_step_f32<false, true, DPT, ZC, R, MAXT, REGS>
         <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);

@@ -196,6 +196,76 @@ lb_rt_status reset_budget(lb_rt* h) {
   return LB_RT_OK;
 }
 
+// nsteps steps; the last one also writes E, F of the new state to mE / mF
+// (FP32 static step only; the caller checks that the epilogue form applies)
+lb_rt_status run_steps(lb_rt* h, int nsteps, float* mE, float* mF) {
+  if (h->timing) CK(h, cudaEventRecord(h->ev0, h->stream));
+  int launches = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    StepLaunch L{};
+    L.g = h->grid;
+    L.N = h->Ni;
+    L.dpt = h->dpt;
+    L.zc = h->zc;
+    L.nzc = h->nzc;
+    L.ctas = h->ctas;
+    L.dt = (float)h->dt;
+    L.collision = h->cfg.collision;
+    L.lambda_iters = h->cfg.lambda_iters;
+    L.in = h->pop[h->cur];
+    L.out = h->pop[h->cur ^ 1];
+    L.tmap_in = h->tmap_ok ? &h->tmap[h->cur] : nullptr;
+    L.tmap_e = h->ef[0] && h->tmap_ok ? &h->emap[h->cur] : nullptr;
+    L.e_in = h->ef[h->cur];
+    L.e_out = h->ef[h->cur ^ 1];
+    L.err = h->err;
+    L.budget_partials = nullptr;
+    L.partials_cap = h->partials_cap;
+    if (s == nsteps - 1) {
+      L.mom_E = mE;
+      L.mom_F = mF;
+    }
+    int nblocks = 0;
+    if (h->cfg.budget) {
+      L.budget_partials = h->partials;
+      CK(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 2 * h->partials_cap, h->stream));
+    }
+    cudaError_t e = h->cfg.moving
+                        ? launch_step_moving(L, h->mc, h->table, h->cfg.storage, h->stream, &nblocks)
+                        : launch_step_static(L, h->sc, h->table, h->cfg.storage, h->stream, &nblocks);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    ++launches;
+    if (h->nfrozen) {
+      e = launch_frozen(h->grid, h->Ni, h->N, h->d_int_of_ext, h->nfrozen, h->frozen_cells,
+                        h->frozen_vals, h->pop[h->cur ^ 1], h->ef[h->cur ^ 1], h->cfg.storage,
+                        h->table, h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
+    }
+    if (h->cfg.budget) {
+      e = launch_budget_finalize(h->partials, nblocks, h->acc, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "budget kernel");
+    }
+    h->cur ^= 1;
+    ++h->steps;
+  }
+  if (h->timing) CK(h, cudaEventRecord(h->ev1, h->stream));
+  h->last_nlaunch = launches;
+  return LB_RT_OK;
+}
+
+// device address the kernels may write for a host pointer: page-locked
+// mapped memory gives one, anything else nullptr
+float* mapped_device_ptr(float* p) {
+  if (!p) return nullptr;
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<float*>(d);
+}
+
+
 }  // namespace
 
 size_t lbrt::handle_device_bytes(const lb_rt_config& cfg, std::string& err) {
@@ -271,8 +341,11 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   if (cfg->dims == 2)
     for (int i = 0; i < h->N; ++i)
       if (h->n[3 * i + 2] != 0.0) return bad("2D grids need directions with n_z == 0");
-  if (cfg->collision != LB_RT_EXPLICIT && !isotropic_table(h->n, h->w, cfg->dims, err))
-    return bad(err.c_str());
+  {
+    std::string iso_err;
+    h->iso = isotropic_table(h->n, h->w, cfg->dims, iso_err);
+    if (cfg->collision != LB_RT_EXPLICIT && !h->iso) return bad(iso_err.c_str());
+  }
   h->grid.nx = cfg->nx;
   h->grid.ny = cfg->ny;
   h->grid.nz = cfg->nz;
@@ -498,56 +571,44 @@ lb_rt_status lb_rt_set_frozen(lb_rt* h, const int64_t* cells, int ncells, const 
   return LB_RT_OK;
 }
 
+
 lb_rt_status lb_rt_step(lb_rt* h, int nsteps) {
   if (!h) return LB_RT_EINVAL;
   if (nsteps < 0) return fail(h, LB_RT_EINVAL, "nsteps < 0");
-  if (h->timing) CK(h, cudaEventRecord(h->ev0, h->stream));
-  int launches = 0;
-  for (int s = 0; s < nsteps; ++s) {
-    StepLaunch L{};
-    L.g = h->grid;
-    L.N = h->Ni;
-    L.dpt = h->dpt;
-    L.zc = h->zc;
-    L.nzc = h->nzc;
-    L.ctas = h->ctas;
-    L.dt = (float)h->dt;
-    L.collision = h->cfg.collision;
-    L.lambda_iters = h->cfg.lambda_iters;
-    L.in = h->pop[h->cur];
-    L.out = h->pop[h->cur ^ 1];
-    L.tmap_in = h->tmap_ok ? &h->tmap[h->cur] : nullptr;
-    L.tmap_e = h->ef[0] && h->tmap_ok ? &h->emap[h->cur] : nullptr;
-    L.e_in = h->ef[h->cur];
-    L.e_out = h->ef[h->cur ^ 1];
-    L.err = h->err;
-    L.budget_partials = nullptr;
-    L.partials_cap = h->partials_cap;
-    int nblocks = 0;
-    if (h->cfg.budget) {
-      L.budget_partials = h->partials;
-      CK(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 2 * h->partials_cap, h->stream));
-    }
-    cudaError_t e = h->cfg.moving
-                        ? launch_step_moving(L, h->mc, h->table, h->cfg.storage, h->stream, &nblocks)
-                        : launch_step_static(L, h->sc, h->table, h->cfg.storage, h->stream, &nblocks);
-    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
-    ++launches;
-    if (h->nfrozen) {
-      e = launch_frozen(h->grid, h->Ni, h->N, h->d_int_of_ext, h->nfrozen, h->frozen_cells,
-                        h->frozen_vals, h->pop[h->cur ^ 1], h->ef[h->cur ^ 1], h->cfg.storage,
-                        h->table, h->cfg.budget ? h->acc + 6 : nullptr, h->stream);
-      if (e != cudaSuccess) return cuda_fail(h, e, "frozen kernel");
-    }
-    if (h->cfg.budget) {
-      e = launch_budget_finalize(h->partials, nblocks, h->acc, h->stream);
-      if (e != cudaSuccess) return cuda_fail(h, e, "budget kernel");
-    }
-    h->cur ^= 1;
-    ++h->steps;
+  return run_steps(h, nsteps, nullptr, nullptr);
+}
+
+lb_rt_status lb_rt_step_moments(lb_rt* h, int nsteps, float* E, float* F, int ptr_kind) {
+  if (!h) return LB_RT_EINVAL;
+  if (nsteps < 0) return fail(h, LB_RT_EINVAL, "nsteps < 0");
+  if (ptr_kind != LB_RT_HOST && ptr_kind != LB_RT_DEVICE)
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
+  const bool epilogue = nsteps > 0 && (E || F) && !h->cfg.moving &&
+                        h->cfg.storage == LB_RT_F32 && h->nfrozen == 0 && h->iso;
+  if (!epilogue) {
+    const lb_rt_status st = run_steps(h, nsteps, nullptr, nullptr);
+    if (st != LB_RT_OK) return st;
+    return lb_rt_moments(h, E, F, nullptr, nullptr, ptr_kind);
   }
-  if (h->timing) CK(h, cudaEventRecord(h->ev1, h->stream));
-  h->last_nlaunch = launches;
+  const long long S = h->grid.sites;
+  float *dE = E, *dF = F;
+  bool stageE = false, stageF = false;
+  if (ptr_kind == LB_RT_HOST) {
+    dE = mapped_device_ptr(E);
+    dF = mapped_device_ptr(F);
+    stageE = E && !dE;
+    stageF = F && !dF;
+    if ((stageE || stageF) && !h->scratch)
+      CK(h, cudaMalloc((void**)&h->scratch, sizeof(float) * 10 * S));
+    if (stageE) dE = h->scratch;
+    if (stageF) dF = h->scratch + S;
+  }
+  const lb_rt_status st = run_steps(h, nsteps, dE, dF);
+  if (st != LB_RT_OK) return st;
+  if (stageE) CK(h, cudaMemcpyAsync(E, dE, sizeof(float) * S, cudaMemcpyDeviceToHost, h->stream));
+  if (stageF)
+    CK(h, cudaMemcpyAsync(F, dF, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+  if (ptr_kind == LB_RT_HOST) return lb_rt_sync(h);
   return LB_RT_OK;
 }
 

@@ -92,6 +92,8 @@ struct StepLaunch {
   double* budget_partials;  // [nblocks][2] (sum E*, sum E_collided) or nullptr
   long long partials_cap;   // slots available; a launcher whose grid is larger refuses
   unsigned* err;            // device error word
+  float* mom_E;             // FP32 static step: E of the new state, dense [sites], or nullptr
+  float* mom_F;             // FP32 static step: F of the new state, dense [3][sites], or nullptr
 };
 
 // One problem of a static step launch.  The single-problem launch passes it
@@ -111,6 +113,8 @@ struct ProblemDesc {
   int nzc;                    // z chunks per column of tiles
   int tile_start, ntiles;
   double* budget_partials;    // single-problem launch only
+  float* mom_E;               // single-problem FP32 launch: E of the new state [sites] or nullptr
+  float* mom_F;               // single-problem FP32 launch: F of the new state [3][sites] or nullptr
 };
 
 // A batched static step: every problem of `table` (device memory) has the

@@ -30,7 +30,7 @@ EXPORTED = [
     "lb_rt_moments", "lb_rt_get_populations", "lb_rt_state_bytes", "lb_rt_save_state",
     "lb_rt_restore_state", "lb_rt_sync", "lb_rt_directions", "lb_rt_enable_timing",
     "lb_rt_last_step_ms", "lb_rt_last_error", "lb_rt_version", "lb_rt_destroy",
-    "lb_rt_total_energy_noalloc", "lb_rt_coupling",
+    "lb_rt_total_energy_noalloc", "lb_rt_coupling", "lb_rt_step_moments",
     "lb_rt_batch_create", "lb_rt_batch_destroy", "lb_rt_batch_problem_bytes", "lb_rt_batch_admit",
     "lb_rt_batch_tick", "lb_rt_batch_sync", "lb_rt_batch_poll", "lb_rt_batch_moments",
     "lb_rt_batch_steps", "lb_rt_batch_release", "lb_rt_batch_tuning", "lb_rt_batch_last_error",
@@ -99,6 +99,7 @@ def load(path=LIB_PATH):
         "lb_rt_set_state": (C.c_int, [H, C.c_void_p, C.c_int, C.c_int]),
         "lb_rt_set_frozen": (C.c_int, [H, C.c_void_p, C.c_int, C.c_void_p]),
         "lb_rt_step": (C.c_int, [H, C.c_int]),
+        "lb_rt_step_moments": (C.c_int, [H, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
         "lb_rt_moments": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.POINTER(lb_rt_budget), C.c_int]),
         "lb_rt_get_populations": (C.c_int, [H, C.c_void_p, C.c_int]),
@@ -304,6 +305,13 @@ def lb_rt_moments(h, E=None, F=None, P=None, budget=False):
     _check(h, load().lb_rt_moments(h, _ptr(E)[0], _ptr(F)[0], _ptr(P)[0],
                                    C.byref(b) if budget else None, kind))
     return b.as_dict() if budget else None
+
+
+def lb_rt_step_moments(h, nsteps, E=None, F=None):
+    """Advance nsteps and fill E [sites], F [3, sites] of the new state from
+    the last step's collision (lb_rt_step_moments)."""
+    kind = _kind_of([E, F])
+    _check(h, load().lb_rt_step_moments(h, int(nsteps), _ptr(E)[0], _ptr(F)[0], kind))
 
 
 def lb_rt_coupling(h, J=None, H=None, S=None):
