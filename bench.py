@@ -7,10 +7,11 @@ faces, kappa_a = eta = 40 inside R = 0.25 (kappa_a R = 10), cfl 0.5.
 Prints one JSON line.  `value` is site-direction updates per second over
 the timed steps (inputs resident in HBM, 705 MB of populations per step,
 larger than L2); `e2e` is the same metric through the C ABI with host
-buffers: every step copies new fluid coefficients (kappa_a, eta) from pinned
-host memory (lb_rt_set_fluid), steps, and returns E and F to pinned host
-memory (lb_rt_step_moments: the step kernel's collision epilogue writes them
-across the host link), as a coupled hydrodynamics code does each step.
+buffers: every step hands new fluid coefficients (kappa_a, eta) over in
+pinned host memory (lb_rt_set_fluid with LB_RT_HOST_MAPPED: the step kernel
+reads them across the host link), steps, and returns E and F to pinned host
+memory (lb_rt_step_moments: the collision epilogue writes them across the
+host link), as a coupled hydrodynamics code does each step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -403,7 +404,7 @@ def main():
         E_h = torch.empty(sites, dtype=torch.float32).pin_memory()
         F_h = torch.empty((3, sites), dtype=torch.float32).pin_memory()
         for _ in range(2):
-            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
+            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h, mapped=True)
             lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         torch.cuda.synchronize()
         _barrier(ws)
@@ -412,7 +413,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h)
+            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h, mapped=True)
             lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         e1.record(stream)
         e1.synchronize()
@@ -443,8 +444,9 @@ def main():
                      "algorithmic_bytes_per_launch": bytes_per_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * sites,
                 "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps,
-                "route": "lb_rt_set_fluid(kappa_a, eta from pinned host) + "
-                         "lb_rt_step_moments(1 step, E and F to pinned host)"},
+                "route": "lb_rt_set_fluid(kappa_a, eta in pinned host memory, read in place "
+                         "by the step kernel) + lb_rt_step_moments(1 step, E and F written "
+                         "to pinned host memory by the step kernel)"},
         "clocks": ck,
         "f16": {"value": sd_step * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
                 "ratio_vs_f32": ms_step / ms16,

@@ -68,7 +68,19 @@ enum {
   LB_RT_EXPLICIT = 1,        /* Eq. (collision-step) */
   LB_RT_LAMBDA_K = 2         /* lambda_iters cycles of the Lambda iteration (Sec. 3.3) */
 };
-enum { LB_RT_HOST = 0, LB_RT_DEVICE = 1 };
+enum {
+  LB_RT_HOST = 0,
+  LB_RT_DEVICE = 1,
+  /* lb_rt_set_fluid only: page-locked host memory the device can address
+   * (cudaHostAlloc, cudaHostRegister with cudaHostRegisterMapped).  The step
+   * kernels read the fields in place across the host link instead of a copy,
+   * so the caller keeps the memory valid and unchanged until every step that
+   * uses it has completed (a later synchronising call) or a later
+   * lb_rt_set_fluid replaces it.  Memory the device cannot address: EINVAL
+   * (where the device translates host page tables, as on coherent CPU-GPU
+   * systems, ordinary pageable memory qualifies too). */
+  LB_RT_HOST_MAPPED = 2
+};
 enum {
   LB_RT_STATE_POPULATIONS = 0, /* N*sites floats, direction-major */
   LB_RT_STATE_ISOTROPIC = 1,   /* sites floats E0: I_i = w_i E0 */
@@ -137,8 +149,12 @@ typedef struct {
 lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out);
 
 /* Copy fluid coefficients (static or moving, per the handle's config) into
- * library storage.  Takes effect for the next lb_rt_step().  Errors: EINVAL
- * (NULL handle/fields, moving fields on a static handle or the reverse). */
+ * library storage, or with ptr_kind = LB_RT_HOST_MAPPED reference them in
+ * page-locked host memory (read in place by the kernels; a coupled fluid
+ * code hands over new fields every step without a copy).  Takes effect for
+ * the next lb_rt_step().  Errors: EINVAL (NULL handle/fields, moving fields
+ * on a static handle or the reverse, LB_RT_HOST_MAPPED memory the device
+ * cannot address). */
 lb_rt_status lb_rt_set_fluid(lb_rt* h, const lb_rt_fluid* f, int ptr_kind);
 
 /* Set the populations (kind = LB_RT_STATE_*), reset the step counter and the
@@ -171,9 +187,10 @@ lb_rt_status lb_rt_moments(lb_rt* h, float* E, float* F, float* P,
  * (Sec. 3.3, Eq. rte_implicit); for an isotropic table (Eq. iso-tensors:
  * sum w = 1, sum w n = 0, sum w n n = Id/d) its moments are E' = alpha E* + c0
  * and F' = alpha F* + c1/d, which the step kernel stores per site.
- * Host pointers to page-locked memory that the device can address
- * (cudaHostAlloc, cudaHostRegister) are written by the step kernel itself
- * across the host link; other host memory goes through a device buffer.
+ * Host memory that the device can address (page-locked memory from
+ * cudaHostAlloc or cudaHostRegister, and on coherent CPU-GPU systems any host
+ * memory) is written by the step kernel itself across the host link; other
+ * host memory goes through a device buffer.
  * With host pointers the call synchronises the stream.  For 16-bit storage,
  * a moving fluid, frozen cells, a table that is not isotropic, or nsteps = 0,
  * it runs lb_rt_step and then lb_rt_moments.  E or F may be NULL.

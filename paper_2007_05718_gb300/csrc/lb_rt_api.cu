@@ -472,10 +472,18 @@ void lb_rt_destroy(lb_rt* h) {
 lb_rt_status lb_rt_set_fluid(lb_rt* h, const lb_rt_fluid* f, int ptr_kind) {
   if (!h) return LB_RT_EINVAL;
   if (!f) return fail(h, LB_RT_EINVAL, "null fluid");
+  if (ptr_kind != LB_RT_HOST && ptr_kind != LB_RT_DEVICE && ptr_kind != LB_RT_HOST_MAPPED)
+    return fail(h, LB_RT_EINVAL, "bad ptr_kind");
   const size_t sb = sizeof(float) * h->grid.sites;
   auto put = [&](int slot, const float* src, size_t bytes, const float** dst) -> lb_rt_status {
     if (!src) {
       *dst = nullptr;
+      return LB_RT_OK;
+    }
+    if (ptr_kind == LB_RT_HOST_MAPPED) {
+      const float* d = mapped_device_ptr(const_cast<float*>(src));
+      if (!d) return fail(h, LB_RT_EINVAL, "LB_RT_HOST_MAPPED field is not page-locked mapped memory");
+      *dst = d;
       return LB_RT_OK;
     }
     if (!h->fld[slot]) CK(h, cudaMalloc((void**)&h->fld[slot], bytes));

@@ -21,7 +21,7 @@ LB_RT_RING2D, LB_RT_ICOSPHERE, LB_RT_GAUSS_LEGENDRE = 1, 2, 3
 LB_RT_PERIODIC, LB_RT_VACUUM = 0, 1
 LB_RT_F32, LB_RT_F16_DEV, LB_RT_BF16_DEV = 0, 1, 2
 LB_RT_IMPLICIT_EXACT, LB_RT_EXPLICIT, LB_RT_LAMBDA_K = 0, 1, 2
-LB_RT_HOST, LB_RT_DEVICE = 0, 1
+LB_RT_HOST, LB_RT_DEVICE, LB_RT_HOST_MAPPED = 0, 1, 2
 LB_RT_STATE_POPULATIONS, LB_RT_STATE_ISOTROPIC, LB_RT_STATE_P1 = 0, 1, 2
 LB_RT_MAX_DIRS = 192
 
@@ -273,9 +273,16 @@ def _make_fluid(kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=None, k
 
 
 def lb_rt_set_fluid(h, kappa_a=0.0, kappa_0=0.0, lam=0.0, eta=0.0, v=None, kt_a=None,
-                    kt_0=None, eta_t=None):
-    """Scalars or float32 site fields [nz, ny, nx] (v: [3, nz, ny, nx])."""
+                    kt_0=None, eta_t=None, mapped=False):
+    """Scalars or float32 site fields [nz, ny, nx] (v: [3, nz, ny, nx]).
+    mapped=True: the fields are page-locked host tensors that the kernels
+    read in place (LB_RT_HOST_MAPPED); the caller keeps them alive and
+    unchanged until the steps that use them have completed."""
     f, kind, keep = _make_fluid(kappa_a, kappa_0, lam, eta, v, kt_a, kt_0, eta_t)
+    if mapped:
+        if kind != LB_RT_HOST:
+            raise ValueError("mapped fields must be host memory")
+        kind = LB_RT_HOST_MAPPED
     _check(h, load().lb_rt_set_fluid(h, C.byref(f), kind))
 
 

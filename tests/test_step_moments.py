@@ -2,7 +2,8 @@
 collision epilogue (E' = alpha E* + c0, F' = alpha F* + c1 / d for an
 isotropic table), against lb_rt_step + lb_rt_moments and the FP64 oracle,
 for every output route (device buffers, page-locked host memory written by
-the kernel, pageable host memory through a device buffer) and for the cases
+the kernel, other host memory written directly where the device addresses it
+and through a device buffer elsewhere) and for the cases
 that fall back to the separate moments pass."""
 import numpy as np
 import pytest
@@ -129,3 +130,38 @@ def test_fallback_cases_equal_the_separate_pass(cuda, case):
     E1, F1, _ = _fused(p, steps, "pageable")
     np.testing.assert_array_equal(E1, E2)
     np.testing.assert_array_equal(F1, F2)
+
+
+def test_fields_read_in_place_from_page_locked_host_memory(cuda):
+    """lb_rt_set_fluid with LB_RT_HOST_MAPPED: the kernels read kappa_a and
+    eta from pinned host memory; the run is bit-identical to copied fields
+    and new field values take effect at the next step."""
+    import torch
+    p = _sphere(24)
+    ka = torch.from_numpy(p.coef["kappa_a"]).pin_memory()
+    eta = torch.from_numpy(p.coef["eta"]).pin_memory()
+    S = int(np.prod(p.shape))
+    h1, h2 = make_handle(p), make_handle(p)
+    try:
+        out = []
+        for h, mapped in ((h1, True), (h2, False)):
+            E = torch.zeros(S, dtype=torch.float32).pin_memory()
+            F = torch.zeros((3, S), dtype=torch.float32).pin_memory()
+            for k in range(3):
+                scale = 1.0 + 0.5 * k
+                if mapped:
+                    ka.copy_(torch.from_numpy(p.coef["kappa_a"] * scale))
+                    lbrt.lb_rt_set_fluid(h, kappa_a=ka, eta=eta, mapped=True)
+                else:
+                    lbrt.lb_rt_set_fluid(h, kappa_a=p.coef["kappa_a"] * scale, eta=p.coef["eta"])
+                lbrt.lb_rt_step_moments(h, 2, E, F)
+            out.append((E.numpy().copy(), F.numpy().copy()))
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        np.testing.assert_array_equal(out[0][1], out[1][1])
+        # an unknown pointer kind is refused
+        import ctypes
+        f, _, keep = lbrt._make_fluid(kappa_a=1.0)
+        assert lbrt.load().lb_rt_set_fluid(h1, ctypes.byref(f), 7) == lbrt.LB_RT_EINVAL
+    finally:
+        lbrt.lb_rt_destroy(h1)
+        lbrt.lb_rt_destroy(h2)
