@@ -51,17 +51,22 @@ struct DirConst {
   int sh, inert, pad0, pad1;
 };
 
-// BATCH = false: one problem, `one` and `tmap1` in the parameter space.
-// BATCH = true: `table[nprob]` in device memory; each CTA copies the
+// MODE 0: one problem, `one` and `tmap1` in the parameter space.
+// MODE 1 (batched): `table[nprob]` in device memory; each CTA copies the
 // descriptor of its current tile into shared memory.
+// MODE 2: as MODE 0, and the coefficient units also store E and F of the
+// new state (one.mom_E, one.mom_F); a separate instantiation keeps the
+// plain step's code unchanged.
 // PER: some problem of the launch has a periodic axis (ghost columns,
 // mirror rows and planes are written by the fast store path); all-vacuum
 // launches use the plain store loop.
-template <bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
+template <int MODE, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
            const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
            const DirTable t) {
+  constexpr bool BATCH = MODE == 1;
+  constexpr bool MOM = MODE == 2;
   constexpr int SLOT = slot_floats<DPT, ZC>();
   static_assert(SLOT >= ZC * 4 * 64, "the partial moments must fit in a consumed slot");
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -318,15 +323,17 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
         if (v) {
           bud_a += E;
           bud_b += cc.Enew;
-          // moments of I' = alpha I* + w (c0 + n . c1) for an isotropic table
-          // (sum w = 1, sum w n = 0, sum w n n = Id / d): E' = alpha E* + c0 =
-          // Enew, F' = alpha F* + c1 / d
-          if (!BATCH && one.mom_E) one.mom_E[((long long)z * ny + y) * nx + x] = cc.Enew;
-          if (!BATCH && one.mom_F) {
+          if constexpr (MOM) {
+            // moments of I' = alpha I* + w (c0 + n . c1) for an isotropic
+            // table (sum w = 1, sum w n = 0, sum w n n = Id / d):
+            // E' = alpha E* + c0 = Enew, F' = alpha F* + c1 / d
             const long long st = ((long long)z * ny + y) * nx + x;
-            one.mom_F[st] = fmaf(cc.alpha, Fx, cc.c1x * inv_d);
-            one.mom_F[gr.sites + st] = fmaf(cc.alpha, Fy, cc.c1y * inv_d);
-            one.mom_F[2 * gr.sites + st] = fmaf(cc.alpha, Fz, cc.c1z * inv_d);
+            if (one.mom_E) one.mom_E[st] = cc.Enew;
+            if (one.mom_F) {
+              one.mom_F[st] = fmaf(cc.alpha, Fx, cc.c1x * inv_d);
+              one.mom_F[gr.sites + st] = fmaf(cc.alpha, Fy, cc.c1y * inv_d);
+              one.mom_F[2 * gr.sites + st] = fmaf(cc.alpha, Fz, cc.c1z * inv_d);
+            }
           }
         }
       }
@@ -503,14 +510,14 @@ size_t step_smem(int G) {
          sizeof(DirConst) * (size_t)G * DPT + 8 * (size_t)G * R + sizeof(double) * 4 * ZC + 16;
 }
 
-template <bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
+template <int MODE, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t set_smem_attr() {
   // the opt-in shared-memory size is a per-device function attribute
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<BATCH, PER, DPT, ZC, R, MAXT, REGS>,
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32<MODE, PER, DPT, ZC, R, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
@@ -519,17 +526,28 @@ cudaError_t set_smem_attr() {
 
 // Resident CTAs per SM; the two boundary specialisations have the same
 // launch bounds and shared memory, the smaller count is returned.
+template <int MODE, int DPT, int ZC, int R, int MAXT, int REGS>
+cudaError_t occupancy_mode(int G, int* per_sm) {
+  int a = 0, b = 0;
+  cudaError_t e = set_smem_attr<MODE, false, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_smem_attr<MODE, true, DPT, ZC, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_f32<MODE, false, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_f32<MODE, true, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  *per_sm = std::min(a, b);
+  return e;
+}
+
+// the single-problem grid serves both the plain and the moments variant
 template <bool BATCH, int DPT, int ZC, int R, int MAXT, int REGS>
 cudaError_t occupancy(int G, int* per_sm) {
+  if (BATCH) return occupancy_mode<1, DPT, ZC, R, MAXT, REGS>(G, per_sm);
   int a = 0, b = 0;
-  cudaError_t e = set_smem_attr<BATCH, false, DPT, ZC, R, MAXT, REGS>();
-  if (e == cudaSuccess) e = set_smem_attr<BATCH, true, DPT, ZC, R, MAXT, REGS>();
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &a, k_step_f32<BATCH, false, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &b, k_step_f32<BATCH, true, DPT, ZC, R, MAXT, REGS>, 32 * G, step_smem<DPT, ZC, R>(G));
+  cudaError_t e = occupancy_mode<0, DPT, ZC, R, MAXT, REGS>(G, &a);
+  if (e == cudaSuccess) e = occupancy_mode<2, DPT, ZC, R, MAXT, REGS>(G, &b);
   *per_sm = std::min(a, b);
   return e;
 }
@@ -548,8 +566,11 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   const size_t smem = step_smem<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   const bool per = any_periodic(L.g);
-  const cudaError_t e = per ? set_smem_attr<false, true, DPT, ZC, R, MAXT, REGS>()
-                            : set_smem_attr<false, false, DPT, ZC, R, MAXT, REGS>();
+  const bool mom = L.mom_E || L.mom_F;
+  const cudaError_t e = mom ? (per ? set_smem_attr<2, true, DPT, ZC, R, MAXT, REGS>()
+                                   : set_smem_attr<2, false, DPT, ZC, R, MAXT, REGS>())
+                            : (per ? set_smem_attr<0, true, DPT, ZC, R, MAXT, REGS>()
+                                   : set_smem_attr<0, false, DPT, ZC, R, MAXT, REGS>());
   if (e != cudaSuccess) return e;
   ProblemDesc one{};
   one.g = L.g;
@@ -565,11 +586,17 @@ cudaError_t launch_f32(const StepLaunch& L, const StaticCoef& c, const DirTable&
   one.budget_partials = L.budget_partials;
   one.mom_E = L.mom_E;
   one.mom_F = L.mom_F;
-  if (per)
-    k_step_f32<false, true, DPT, ZC, R, MAXT, REGS>
+  if (mom && per)
+    k_step_f32<2, true, DPT, ZC, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
+  else if (mom)
+    k_step_f32<2, false, DPT, ZC, R, MAXT, REGS>
+        <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
+  else if (per)
+    k_step_f32<0, true, DPT, ZC, R, MAXT, REGS>
         <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
   else
-    k_step_f32<false, false, DPT, ZC, R, MAXT, REGS>
+    k_step_f32<0, false, DPT, ZC, R, MAXT, REGS>
         <<<L.ctas, dim3(32, G), smem, s>>>(*L.tmap_in, one, nullptr, 1, one.ntiles, L.err, t);
   return cudaGetLastError();
 }
@@ -582,17 +609,17 @@ cudaError_t launch_f32_batch(const BatchLaunch& B, const DirTable& t, cudaStream
     return cudaErrorInvalidValue;
   const size_t smem = step_smem<DPT, ZC, R>(G);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
-  const cudaError_t e = B.periodic ? set_smem_attr<true, true, DPT, ZC, R, MAXT, REGS>()
-                                   : set_smem_attr<true, false, DPT, ZC, R, MAXT, REGS>();
+  const cudaError_t e = B.periodic ? set_smem_attr<1, true, DPT, ZC, R, MAXT, REGS>()
+                                   : set_smem_attr<1, false, DPT, ZC, R, MAXT, REGS>();
   if (e != cudaSuccess) return e;
   // the parameter-space tensor map and descriptor are unused by the batched kernel
   CUtensorMap unused{};
   ProblemDesc none{};
   if (B.periodic)
-    k_step_f32<true, true, DPT, ZC, R, MAXT, REGS>
+    k_step_f32<1, true, DPT, ZC, R, MAXT, REGS>
         <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   else
-    k_step_f32<true, false, DPT, ZC, R, MAXT, REGS>
+    k_step_f32<1, false, DPT, ZC, R, MAXT, REGS>
         <<<B.ctas, dim3(32, G), smem, s>>>(unused, none, B.table, B.nprob, B.ntiles, B.err, t);
   return cudaGetLastError();
 }
