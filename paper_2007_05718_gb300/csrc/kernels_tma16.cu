@@ -577,7 +577,10 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
   unsigned char* ring = smem_raw;
   float* ering = reinterpret_cast<float*>(ring + (size_t)G * R * SLOTB);
   float* coef = ering + R * ESLOT;  // [2][64]: src, 1 / E^'
-  DirConstM16* dirs = reinterpret_cast<DirConstM16*>(coef + 2 * 64);
+  // per-site fields (vx, vy, vz, kt_a, kt_0, eta_t) of the current and the
+  // next item, copied in by the last warp one item ahead
+  float* fbuf = coef + 2 * 64;
+  DirConstM16* dirs = reinterpret_cast<DirConstM16*>(fbuf + 2 * 6 * 64);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(dirs + G * DPT);
   unsigned long long* ebar = mbar + G * R;
   double* bsum = reinterpret_cast<double*>(ebar + R);
@@ -617,6 +620,33 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
       for (int r = 0; r < R; ++r) mbar_init(smem_u32(&ebar[r]), 1);
   }
   if (g == 0 && lane == 0) *abort_flag = 0;
+  // fields of item (tile tix, item mm) into fbuf[b]: invalid sites read
+  // site 0, absent fields take their scalar (velocity 0)
+  auto stage = [&](int tix, int mm, int b) {
+    const TileGeom tq = tile_geom(tix, nxb, ny, nz, L.nzc);
+    const int zq = tq.zbeg - 1 + mm;
+    const bool zokq = zq >= tq.zbeg && zq < tq.zbeg + tq.zlen;
+    float* dst = fbuf + b * 6 * 64;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int f = 2 * lane + h, x = tq.x0 + f;
+      const long long st = zokq && x < nx ? ((long long)zq * ny + tq.y) * nx + x : 0;
+      auto put = [&](int c, const float* p, long long off, float sc) {
+        if (p) cp_async4(dst + c * 64 + f, p + off);
+        else dst[c * 64 + f] = sc;
+      };
+      put(0, mc.v, st, 0.f);
+      put(1, mc.v, sites + st, 0.f);
+      put(2, mc.v, 2 * sites + st, 0.f);
+      put(3, mc.kta, st, mc.kta_s);
+      put(4, mc.kt0, st, mc.kt0_s);
+      put(5, mc.etat, st, mc.etat_s);
+    }
+  };
+  if (g == G - 1 && (int)blockIdx.x < ntiles) {
+    stage(blockIdx.x, 0, 0);
+    cp_async_wait_all();
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   unsigned inert_mask = 0;
@@ -704,27 +734,26 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     for (int m = 0; m < M; ++m, ++q) {
       const int z = zbeg - 1 + m;
       const bool zok = z >= zbeg && z < zend;
+      if (g == G - 1) {
+        int tn = ti, mn = m + 1;
+        if (mn == M) {
+          tn = ti + gridDim.x;
+          mn = 0;
+        }
+        if (tn < ntiles) stage(tn, mn, (q + 1) & 1);
+      }
+      const float* fb = fbuf + (q & 1) * 6 * 64;
       float2 vx, vy, vz, W, cA, et;
       {
-        float a[2][6];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const bool v = zok && (xa + h < nx);
-          const long long st = v ? ((long long)z * ny + y) * nx + xa + h : 0;
-          a[h][0] = mc.v ? __ldg(mc.v + st) : 0.f;
-          a[h][1] = mc.v ? __ldg(mc.v + sites + st) : 0.f;
-          a[h][2] = mc.v ? __ldg(mc.v + 2 * sites + st) : 0.f;
-          a[h][3] = fld(mc.kta, mc.kta_s, st);
-          a[h][4] = fld(mc.kt0, mc.kt0_s, st);
-          a[h][5] = fld(mc.etat, mc.etat_s, st);
-        }
-        vx = make_float2(a[0][0], a[1][0]);
-        vy = make_float2(a[0][1], a[1][1]);
-        vz = make_float2(a[0][2], a[1][2]);
+        const float2* f2 = reinterpret_cast<const float2*>(fb) + lane;
+        vx = f2[0];
+        vy = f2[32];
+        vz = f2[64];
+        const float2 ka = f2[96], k0 = f2[128];
+        et = f2[160];
         const float2 v2 = f2fma(vz, vz, f2fma(vy, vy, f2mul(vx, vx)));
         W = make_float2(rsqrtf(1.f - v2.x), rsqrtf(1.f - v2.y));
-        cA = f2mul(f2mul(make_float2(dt, dt), W), make_float2(a[0][3] + a[0][4], a[1][3] + a[1][4]));
-        et = make_float2(a[0][5], a[1][5]);
+        cA = f2mul(f2mul(make_float2(dt, dt), W), make_float2(ka.x + k0.x, ka.y + k0.y));
       }
       // beta_i, A_i and g'_i = A_i dt (W beta_i)^-3 for direction constants d
       auto coll = [&](const DirConstM16& d, float2& beta, float2& A, float2& gp) {
@@ -796,16 +825,17 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
         p[96] = aA;
         p[128] = aG;
       }
+      // the next item's fields have landed before the barrier that publishes them
+      if (g == G - 1) cp_async_wait_all();
       __syncthreads();
       for (int u = g; u < nunits; u += G) {
         const int f = (u << 5) + lane;
         const int x = x0 + f;
         const bool v = zok && x < nx;
         const long long st = v ? ((long long)z * ny + y) * nx + x : 0;
-        const float ux = mc.v ? __ldg(mc.v + st) : 0.f;
-        const float uy = mc.v ? __ldg(mc.v + sites + st) : 0.f;
-        const float uz = mc.v ? __ldg(mc.v + 2 * sites + st) : 0.f;
-        const float kt0 = fld(mc.kt0, mc.kt0_s, st), etat = fld(mc.etat, mc.etat_s, st);
+        (void)st;
+        const float ux = fb[f], uy = fb[64 + f], uz = fb[128 + f];
+        const float kt0 = fb[256 + f], etat = fb[320 + f];
         const int s = q % R;
         float S = 0.f, X = 0.f, Y = 0.f, SA = 0.f, SG = 0.f;
         for (int qq = 0; qq < G; ++qq) {
@@ -915,7 +945,7 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
 template <int DPT, int R>
 size_t smem_moving16(int G) {
   return (size_t)G * R * slot_bytes16<DPT, 1>() +
-         sizeof(float) * ((size_t)R * eslot_floats<1>() + 2 * 64) +
+         sizeof(float) * ((size_t)R * eslot_floats<1>() + 2 * 64 + 2 * 6 * 64) +
          sizeof(DirConstM16) * (size_t)G * DPT + 8 * ((size_t)G * R + R) + sizeof(double) * 4 + 16;
 }
 

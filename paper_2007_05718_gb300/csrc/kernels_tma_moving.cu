@@ -39,16 +39,6 @@ __device__ __forceinline__ float2 f2rcp(float2 a) {
   return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y));
 }
 
-// 4-byte global -> shared copy that completes asynchronously (cp.async);
-// cp_async_wait_all() waits for all of the thread's outstanding copies
-__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 template <bool PER, int DPT, int R, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_moving_tma(const __grid_constant__ CUtensorMap tmap, const StepLaunch L,

@@ -83,6 +83,16 @@ __device__ __forceinline__ float fld(const float* __restrict__ p, float s, long 
   return p ? __ldg(p + i) : s;
 }
 
+// 4-byte global -> shared copy that completes asynchronously (cp.async);
+// cp_async_wait_all() waits for all of the thread's outstanding copies
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 struct Coef {
   float alpha, c0, c1x, c1y, c1z, Enew;
 };
