@@ -97,15 +97,27 @@ class Clocks:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # wait (up to 5 s) until the sampler runs, and count only the samples
+        # taken from here on, i.e. during the timed region
+        self.skip = 0
+        if self.proc:
+            t_end = time.time() + 5.0
+            while time.time() < t_end:
+                self.f.flush()
+                n = sum(1 for _ in open(self.path))
+                if n > 0:
+                    self.skip = n
+                    break
+                time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
             return None
-        time.sleep(0.25)
+        time.sleep(0.06)  # one more sample interval
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -114,7 +126,9 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for i, line in enumerate(open(self.path)):
+            if i < self.skip:
+                continue
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -321,7 +335,7 @@ def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
