@@ -70,3 +70,10 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.lb_rt_sync(None) == lbrt.LB_RT_EINVAL
     lib.lb_rt_destroy(None)
     assert lib.lb_rt_state_bytes(None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without liblbrt.so every call raises."""
+    monkeypatch.setattr(lbrt, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        lbrt.load(str(tmp_path / "liblbrt.so"))
