@@ -306,6 +306,42 @@ def moving_fluid_costs(n=256, level=2, steps=10, warmup=3):
     return out
 
 
+def diffusion_costs(n=256, level=2, steps=10, warmup=3):
+    """Optically thick diffusion, 256^3 x 162 periodic, kappa_0 = 1e3 /L,
+    Gaussian E0 (sigma 8 cells): step time with FP32, FP16 and BF16
+    populations, and the 16-bit over FP32 rate."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    E0 = torch.from_numpy(W.gaussian_E0((n, n, n), 8.0)).cuda()
+    out = {}
+    for name, st in (("fp32", lbrt.LB_RT_F32), ("fp16", lbrt.LB_RT_F16_DEV),
+                     ("bf16", lbrt.LB_RT_BF16_DEV)):
+        stream = torch.cuda.Stream()
+        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=level, cfl=CFL,
+                              dx=1.0 / n, bc=(lbrt.LB_RT_PERIODIC,) * 3, storage=st,
+                              stream=stream.cuda_stream)
+        lbrt.lb_rt_set_fluid(h, kappa_0=1000.0)
+        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        lbrt.lb_rt_step(h, warmup)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lbrt.lb_rt_step(h, steps)
+        b.record(stream)
+        b.synchronize()
+        lbrt.lb_rt_sync(h)
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_step": ms, "sd_s": n ** 3 * N / (ms * 1e-3)}
+        lbrt.lb_rt_destroy(h)
+        torch.cuda.empty_cache()
+    out["fp16_over_fp32"] = out["fp32"]["ms_per_step"] / out["fp16"]["ms_per_step"]
+    out["bf16_over_fp32"] = out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
+    out["workload"] = "256^3 x 162 periodic diffusion, kappa_0 = 1e3 /L, Gaussian E0 (8 cells)"
+    return out
+
+
 def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
     """Batched serving on the seeded request stream (sphere/shadow, n in
     {32..128}^3, 42 or 162 directions, kappa log-uniform 1e-1..1e4, 200-2000
@@ -473,6 +509,10 @@ def main():
         except Exception as e:  # report, do not hide
             line["collision_modes"] = {"error": str(e)[:300]}
     if not args.no_moving and ws == 1:
+        try:
+            line["diffusion_256"] = diffusion_costs()
+        except Exception as e:  # report, do not hide
+            line["diffusion_256"] = {"error": str(e)[:300]}
         try:
             line["moving_fluid"] = moving_fluid_costs()
         except Exception as e:  # report, do not hide
