@@ -261,6 +261,12 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
     const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
     const bool gx_hi = gr.periodic[0] && xa == 0;
     const bool lo_from_y = xa + 1 == nx - 1;
+    // fast path (every lane a full pair, so no lane holds both x = 0 and
+    // x = nx - 1): the lane's one ghost-column store as offset, value select
+    // and predicate
+    const bool gx_any = gx_lo || gx_hi;
+    const int gx_off = gx_lo ? GL - 1 - (xa + GL) : nx + GL - (xa + GL);
+    const bool gx_y = gx_lo && lo_from_y;
     const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
     ST* const orow = out + (long long)i0 * gr.si + (long long)(y + 1) * gr.sy + xa + GL;
     for (int m = 0; m < M; ++m, ++q) {
@@ -466,10 +472,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
               const T2 h = C2::from2(qn);
               auto put = [&](ST* d) {
                 *reinterpret_cast<T2*>(d) = h;
-                if (xghost) {  // warp-uniform
-                  if (gx_lo) d[GL - 1 - (xa + GL)] = lo_from_y ? h.y : h.x;
-                  if (gx_hi) d[nx + GL - (xa + GL)] = h.x;
-                }
+                if (xghost && gx_any) d[gx_off] = gx_y ? h.y : h.x;  // one predicated store
               };
               put(dst);
               if (y_face) put(dst + (long long)yface_rows * gr.sy);  // warp-uniform
@@ -729,6 +732,12 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
     const bool gx_hi = gr.periodic[0] && xa == 0;
     const bool lo_from_y = xa + 1 == nx - 1;
+    // fast path (every lane a full pair, so no lane holds both x = 0 and
+    // x = nx - 1): the lane's one ghost-column store as offset, value select
+    // and predicate
+    const bool gx_any = gx_lo || gx_hi;
+    const int gx_off = gx_lo ? GL - 1 - (xa + GL) : nx + GL - (xa + GL);
+    const bool gx_y = gx_lo && lo_from_y;
     const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
     ST* const orow = out + (long long)i0 * gr.si + (long long)(y + 1) * gr.sy + xa + GL;
     for (int m = 0; m < M; ++m, ++q) {
@@ -887,10 +896,7 @@ k_step_moving16(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
           } else {
             auto put = [&](ST* dd) {
               *reinterpret_cast<T2*>(dd) = hq;
-              if (xghost) {
-                if (gx_lo) dd[GL - 1 - (xa + GL)] = lo_from_y ? hq.y : hq.x;
-                if (gx_hi) dd[nx + GL - (xa + GL)] = hq.x;
-              }
+              if (xghost && gx_any) dd[gx_off] = gx_y ? hq.y : hq.x;  // one predicated store
             };
             put(dst);
             if (y_face) put(dst + (long long)yface_rows * gr.sy);

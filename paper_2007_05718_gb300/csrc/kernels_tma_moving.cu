@@ -192,6 +192,12 @@ k_step_moving_tma(const __grid_constant__ CUtensorMap tmap, const StepLaunch L,
     const bool gx_lo = gr.periodic[0] && (xa == nx - 1 || xa + 1 == nx - 1);
     const bool gx_hi = gr.periodic[0] && xa == 0;
     const bool lo_from_y = xa + 1 == nx - 1;
+    // fast path (every lane a full pair, so no lane holds both x = 0 and
+    // x = nx - 1): the lane's one ghost-column store as offset, value select
+    // and predicate
+    const bool gx_any = gx_lo || gx_hi;
+    const int gx_off = gx_lo ? GL - 1 - (xa + GL) : nx + GL - (xa + GL);
+    const bool gx_y = gx_lo && lo_from_y;
     const bool y_face = gr.periodic[1] && (y == 0 || y == ny - 1);
     float* const orow = out + (long long)i0 * gr.si + (long long)(y + 1) * gr.sy + xa + GL;
     for (int m = 0; m < M; ++m, ++q) {
@@ -333,10 +339,7 @@ k_step_moving_tma(const __grid_constant__ CUtensorMap tmap, const StepLaunch L,
           } else {
             auto put = [&](float* dd) {
               *reinterpret_cast<float2*>(dd) = o;
-              if (xghost) {
-                if (gx_lo) dd[GL - 1 - (xa + GL)] = lo_from_y ? o.y : o.x;
-                if (gx_hi) dd[nx + GL - (xa + GL)] = o.x;
-              }
+              if (xghost && gx_any) dd[gx_off] = gx_y ? o.y : o.x;  // one predicated store
             };
             put(dst);
             if (y_face) put(dst + (long long)yface_rows * gr.sy);
