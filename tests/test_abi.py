@@ -67,6 +67,8 @@ def test_invalid_configs_rejected_before_cuda(lib, kw, frag):
 
 def test_null_handle_calls_are_safe(lib):
     assert lib.lb_rt_step(None, 1) == lbrt.LB_RT_EINVAL
+    assert lib.lb_rt_step_moments(None, 1, None, None, lbrt.LB_RT_HOST) == lbrt.LB_RT_EINVAL
+    assert lib.lb_rt_coupling(None, None, None, None, lbrt.LB_RT_HOST) == lbrt.LB_RT_EINVAL
     assert lib.lb_rt_sync(None) == lbrt.LB_RT_EINVAL
     lib.lb_rt_destroy(None)
     assert lib.lb_rt_state_bytes(None) == 0
