@@ -20,12 +20,20 @@ lb          one timestep (Sec. 3.3): pull-streaming with the trilinear /
             (App. B), frozen cells, and the energy budget.
 analytic    closed-form references: radiating sphere (Sec. 4.2.2), Gaussian
             diffusion (Eq. gauss-hill-analytic with the diffusion coefficient
-            of App. A), and the dense N x N brute-force collision solve.
+            of App. A), the free-streaming radiation wave (Sec. 4.1.2), and
+            the dense N x N brute-force collision solve.
+coupling    comoving J, H and the radiative four-force (S_0, S_j) of the
+            coupling with a fluid code (Sec. 5, Eq. J).
+diffusion   the diffusion coefficient of the scheme (App. A): exact
+            spatial-moment recursion, closed form, the Gaussian-hill fit of
+            App. A.2 and the fit of Eq. (numerical-diff-coeff2).
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: isotropy identities, the binomial closed form of free streaming,
 the exact CFL = 1 shift, linearity, brute-force dense solves, conservation
 under pure scattering, the radiating-sphere and Gaussian-diffusion analytic
-solutions, and the paper's statement that the Lambda iteration converges in
-at most three cycles for kappa_a = 1e7.
+solutions, the paper's statement that the Lambda iteration converges in
+at most three cycles for kappa_a = 1e7, Lorentz boosts of known comoving
+states, the exact energy and second-moment identities of the free-streaming
+wave, and brute-force lattice runs for the moment recursion.
 """
