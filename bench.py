@@ -375,11 +375,13 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-collision-modes", action="store_true")
-    ap.add_argument("--no-moving", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=20, help="coupled steps of the end-to-end run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched serving run")
+    ap.add_argument("--no-collision-modes", action="store_true",
+                    help="skip the implicit / explicit / Lambda-5 timing")
+    ap.add_argument("--no-moving", action="store_true",
+                    help="skip the 256^3 x 162 runs (diffusion FP32/FP16/BF16, moving fluid)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
