@@ -165,3 +165,15 @@ def test_fields_read_in_place_from_page_locked_host_memory(cuda):
     finally:
         lbrt.lb_rt_destroy(h1)
         lbrt.lb_rt_destroy(h2)
+
+
+def test_full_size_bench_problem(cuda):
+    """The bench's 128^3 x 42 radiating sphere (vacuum faces, kappa_a R = 10):
+    the epilogue moments written to pinned host memory agree with the
+    separate moments pass after the same steps."""
+    p = _sphere(128)
+    E2, F2, I2 = _plain(p, 3)
+    E1, F1, I1 = _fused(p, 3, "pinned")
+    np.testing.assert_array_equal(I1, I2)
+    assert rel_l2(E1, E2) < 2e-6
+    assert np.linalg.norm(F1 - F2) / np.linalg.norm(E2) < 2e-6
