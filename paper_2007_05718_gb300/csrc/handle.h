@@ -47,6 +47,7 @@ struct lb_rt {
   int partials_cap = 0;
   double* acc = nullptr;       // 8 doubles, see k_budget_finalize
   unsigned* err = nullptr;     // device error word
+  unsigned* err_host = nullptr;  // page-locked host copy of it, read after each sync
   float* scratch = nullptr;    // moments staging for host outputs [10][sites]
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timing = false;

@@ -398,6 +398,7 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
   alloc((void**)&h->acc, sizeof(double) * 8);
   alloc((void**)&h->d_int_of_ext, sizeof(int) * h->N);
   alloc((void**)&h->err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->err_host, sizeof(unsigned), cudaHostAllocDefault);
   if (e != cudaSuccess) {
     g_create_msg = std::string("allocation: ") + cudaGetErrorString(e);
     lb_rt_destroy(h);
@@ -462,6 +463,7 @@ void lb_rt_destroy(lb_rt* h) {
   cudaFree(h->acc);
   cudaFree(h->d_int_of_ext);
   cudaFree(h->err);
+  if (h->err_host) cudaFreeHost(h->err_host);
   cudaFree(h->scratch);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -622,9 +624,10 @@ lb_rt_status lb_rt_step_moments(lb_rt* h, int nsteps, float* E, float* F, int pt
 
 lb_rt_status lb_rt_sync(lb_rt* h) {
   if (!h) return LB_RT_EINVAL;
+  // the error word comes back with the same synchronisation
+  CK(h, cudaMemcpyAsync(h->err_host, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  unsigned word = 0;
-  CK(h, cudaMemcpy(&word, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  const unsigned word = *h->err_host;
   if (word) {
     char buf[96];
     std::snprintf(buf, sizeof buf, "device error word 0x%08x", word);
