@@ -168,8 +168,17 @@ lb_rt_status lb_rt_set_state(lb_rt* h, const float* data, int kind, int ptr_kind
  * ncells == 0 clears the list.  Arrays are host arrays, copied. */
 lb_rt_status lb_rt_set_frozen(lb_rt* h, const int64_t* cells, int ncells, const float* values);
 
-/* Enqueue nsteps timesteps on the handle's stream (stream, collide, frozen
- * overwrite, budget).  nsteps >= 0.  Returns launch errors only. */
+/* Enqueue nsteps timesteps on the handle's stream.  One step is the fused
+ * pull-stream and collision of Sec. 3.3: the populations are streamed along
+ * their directions with the trilinear (bilinear in 2D) interpolation of
+ * Eq. interp, then relaxed by the collision chosen at create -- the exact
+ * implicit step of Eq. rte_implicit (closed form of its fixed point), the
+ * explicit step of Eq. collision-step, or a fixed number of Lambda
+ * iterations -- or, for a moving fluid, the mixed-frame implicit step of
+ * App. B.  Then frozen cells are overwritten (Sec. 4.1.1) and, with
+ * config.budget = 1, the FP64 energy budget is updated.  nsteps >= 0.
+ * Asynchronous: returns launch errors only; device-side errors (a bounded
+ * wait that gave up) surface at the next lb_rt_sync(). */
 lb_rt_status lb_rt_step(lb_rt* h, int nsteps);
 
 /* Moments of the current populations (Eqs. moments_discrete, higher_moments):
@@ -202,9 +211,11 @@ lb_rt_status lb_rt_step_moments(lb_rt* h, int nsteps, float* E, float* F, int pt
 /* Coupling outputs of the current state for a fluid code (Sec. 5, step 4 of
  * the coupling): the comoving radiation energy density J [sites] and
  * momentum density H [3][sites] (Eq. J), and the radiative four-force
- * S [4][sites] = (S_0, S_x, S_y, S_z) with S_0 = W (kt_a J - eta_t) + kt H_0,
- * S_j = W (kt_a J - eta_t) v_j + kt H_j, kt = kt_a + kt_0, H_0 = -v.H (from
- * H_mu u^mu = 0, signature -+++).  A static handle uses v = 0 and its static
+ * S [4][sites] = (S_0, S_x, S_y, S_z) with S_0 = W (kt_a J - eta_t) + kt H^0,
+ * S_j = W (kt_a J - eta_t) v_j + kt H_j, kt = kt_a + kt_0: the lab components
+ * of the four-vector (kt_a J - eta_t) u^mu + kt H^mu, u^mu = W (1, v), whose
+ * comoving flux H^mu has the time component H^0 = v.H fixed by
+ * H^mu u_mu = 0 (signature -+++).  A static handle uses v = 0 and its static
  * opacities.  Any output may be NULL.  With host pointers the call
  * synchronises the stream.  Errors: EINVAL, ECUDA. */
 lb_rt_status lb_rt_coupling(lb_rt* h, float* J, float* H, float* S, int ptr_kind);
@@ -220,7 +231,12 @@ size_t lb_rt_state_bytes(const lb_rt* h);
 lb_rt_status lb_rt_save_state(lb_rt* h, void* buf, size_t bytes);
 lb_rt_status lb_rt_restore_state(lb_rt* h, const void* buf, size_t bytes);
 
-/* Wait for the handle's stream; returns the first device-side or CUDA error. */
+/* Wait for the handle's stream; returns the first device-side or CUDA error.
+ * LB_RT_ETIMEDOUT means a bounded wait inside a step kernel gave up: the
+ * populations written since the previous successful lb_rt_sync() are not
+ * trusted.  The device error word is cleared when it is reported, so the
+ * handle stays usable after lb_rt_restore_state() or lb_rt_set_state();
+ * stepping on without either continues from an undefined state. */
 lb_rt_status lb_rt_sync(lb_rt* h);
 
 /* Direction table in the canonical order the library uses: dirs [N*3],
@@ -289,7 +305,9 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
  * first waits for the previous tick, whose tables it reuses). */
 lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active);
 
-/* Wait for the enqueued ticks and surface device errors. */
+/* Wait for the enqueued ticks and surface device errors.  LB_RT_ETIMEDOUT
+ * (a bounded wait in a batched step gave up) leaves every active problem's
+ * state untrusted and the batch's error word set: destroy the batch. */
 lb_rt_status lb_rt_batch_sync(lb_rt_batch* b);
 
 /* Slots whose problems have run all their steps and are not yet released
@@ -327,8 +345,13 @@ const char* lb_rt_batch_last_error(const lb_rt_batch* b);
  * or a host pointer (LB_RT_HOST: the call synchronises `stream`).  The first
  * call on a device looks up the array's device address; make that first call
  * before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (for example on two streams) race.  Errors: EINVAL (bad
- * argument or too many sites), ECUDA; lb_rt_last_error(NULL) says which. */
+ * overlap on the GPU (for example on two streams) race.  The device address
+ * is cached per device ordinal for the life of the process: do not use this
+ * entry point across cudaDeviceReset() or from a context other than the
+ * device's primary context.  pop (and out with LB_RT_DEVICE) must be device
+ * or managed memory; anything else returns LB_RT_EINVAL before a launch.
+ * Errors: EINVAL (bad argument, host memory where device memory is required,
+ * or too many sites), ECUDA; lb_rt_last_error(NULL) says which. */
 lb_rt_status lb_rt_total_energy_noalloc(const float* pop, int ndir, long long sites, double* out,
                                         int ptr_kind, void* stream);
 

@@ -629,6 +629,10 @@ lb_rt_status lb_rt_sync(lb_rt* h) {
   CK(h, cudaStreamSynchronize(h->stream));
   const unsigned word = *h->err_host;
   if (word) {
+    // reported once: the word is cleared so that a restored or re-set state
+    // can be stepped again (the state itself is not trusted, see lb_rt.h)
+    *h->err_host = 0;
+    CK(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
     char buf[96];
     std::snprintf(buf, sizeof buf, "device error word 0x%08x", word);
     return fail(h, LB_RT_ETIMEDOUT, buf);

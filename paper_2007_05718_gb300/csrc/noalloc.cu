@@ -81,6 +81,19 @@ extern "C" lb_rt_status lb_rt_total_energy_noalloc(const float* pop, int ndir, l
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return bad(LB_RT_ECUDA, cudaGetErrorString(e));
+  // the kernels dereference pop (and out for a device result): a host
+  // pointer would fault on the GPU, so it is refused here
+  auto device_reachable = [](const void* q) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  };
+  if (!device_reachable(pop)) return bad(LB_RT_EINVAL, "pop is not device or managed memory");
+  if (ptr_kind == LB_RT_DEVICE && !device_reachable(out))
+    return bad(LB_RT_EINVAL, "out is not device or managed memory (ptr_kind LB_RT_DEVICE)");
   if (dev < 0 || dev >= kMaxDevices) return bad(LB_RT_ECUDA, "device ordinal out of range");
   double* scratch = nullptr;
   {

@@ -388,6 +388,27 @@ def lb_rt_total_energy_noalloc(pop, ndir, sites, out=None, stream=None):
     without any allocation inside the library.  With out=None the result is
     returned as a Python float (host output); otherwise `out` is a float64
     CUDA tensor of one element that receives it on the device."""
+    # every check comes before the C call: a wrong dtype or a short tensor
+    # would make the reduction kernel read or write past the allocation
+    if not type(pop).__module__.startswith("torch"):
+        raise ValueError("populations must be a CUDA tensor")
+    import torch
+    if pop.dtype != torch.float32:
+        raise ValueError("populations must be float32")
+    if not pop.is_contiguous():
+        raise ValueError("populations must be contiguous")
+    if int(ndir) < 1 or int(sites) < 1:
+        raise ValueError("ndir and sites must be >= 1")
+    if pop.numel() < int(ndir) * int(sites):
+        raise ValueError("populations hold %d values, fewer than ndir x sites = %d"
+                         % (pop.numel(), int(ndir) * int(sites)))
+    if out is not None:
+        if not type(out).__module__.startswith("torch"):
+            raise ValueError("out must be a CUDA tensor")
+        if out.dtype != torch.float64 or out.numel() < 1 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of at least one element")
+        if not out.is_cuda:
+            raise ValueError("out must be a CUDA tensor")
     p, pk = _ptr(pop)
     if pk != LB_RT_DEVICE:
         raise ValueError("populations must be a CUDA tensor")

@@ -40,16 +40,38 @@ def test_noalloc_total_matches_regular_reduction(cuda, shape, level):
         lbrt.lb_rt_total_energy_noalloc(pops, N, sites, out=out)
         torch.cuda.synchronize()
         second = float(out.item())
+        # an independent FP64 sum of the very same array, on the host
+        host_sum = float(np.sum(pops.cpu().numpy().astype(np.float64)))
     finally:
         lbrt.lb_rt_destroy(h)
     assert abs(first - expected) <= TOL_F32 * abs(expected)
     assert abs(second - expected) <= TOL_F32 * abs(expected)
+    # the kernel sums a site's directions in float32, then sites in FP64
+    assert abs(first - host_sum) <= TOL_F32 * abs(host_sum)
+    assert abs(second - host_sum) <= TOL_F32 * abs(host_sum)
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments(cuda):
+    """The C entry point itself refuses, before any launch, sizes beyond its
+    fixed scratch array, a zero direction count and host memory where it
+    needs device memory (called here through the raw C ABI, since the
+    binding refuses most of these on its own)."""
+    import ctypes as C
     import torch
+    lib = lbrt.load()
     pops = torch.zeros((1, 8), device="cuda", dtype=torch.float32)
-    with pytest.raises(lbrt.LBRTError):
-        lbrt.lb_rt_total_energy_noalloc(pops, 1, 16_777_217)
-    with pytest.raises(lbrt.LBRTError):
-        lbrt.lb_rt_total_energy_noalloc(pops, 0, 8)
+    res = C.c_double()
+    st = lib.lb_rt_total_energy_noalloc(pops.data_ptr(), 1, 16_777_217, C.byref(res),
+                                        lbrt.LB_RT_HOST, None)
+    assert st == lbrt.LB_RT_EINVAL and "limit" in lbrt.lb_rt_last_error(None)
+    st = lib.lb_rt_total_energy_noalloc(pops.data_ptr(), 0, 8, C.byref(res), lbrt.LB_RT_HOST, None)
+    assert st == lbrt.LB_RT_EINVAL
+    host = np.zeros(8, dtype=np.float32)
+    st = lib.lb_rt_total_energy_noalloc(host.ctypes.data, 1, 8, C.byref(res), lbrt.LB_RT_HOST, None)
+    assert st == lbrt.LB_RT_EINVAL and "device" in lbrt.lb_rt_last_error(None)
+    hout = np.zeros(1, dtype=np.float64)
+    st = lib.lb_rt_total_energy_noalloc(pops.data_ptr(), 1, 8, hout.ctypes.data,
+                                        lbrt.LB_RT_DEVICE, None)
+    assert st == lbrt.LB_RT_EINVAL
+    # a valid call still works after the refusals
+    assert lbrt.lb_rt_total_energy_noalloc(pops, 1, 8) == 0.0
