@@ -12,8 +12,15 @@ and the radiative four-force source terms
   S_0 = W (kt_a J - eta_t) + kt H_0,
   S_j = W (kt_a J - eta_t) v_j + kt H_j,   kt = kt_a + kt_s,  kt_s = kt_0 - kt_1 / 3.
 
-H_0 follows from H_mu u^mu = 0 (reading: metric signature (-, +, +, +),
-u^mu = W (1, v), so H_0 = -v^j H_j).  This scheme keeps kt_1 = 0.
+Reading of the index placement: (S_0, S_j) are the lab-frame components of
+ONE four-vector, G^mu = (kt_a J - eta_t) u^mu + kt H^mu, with u^mu = W (1, v)
+and H^mu the comoving flux four-vector (H^mu u_mu = 0, signature (-, +, +, +)).
+Its spatial part is the printed S_j; its time part is W (kt_a J - eta_t) +
+kt H^0 with H^0 = v^j H_j, the time component fixed by the orthogonality the
+paper names.  (Taking H_0 as the covariant component -v^j H_j would make S_0
+and S_j parts of no single four-vector.)  In the fluid rest frame G reduces
+to (kt_a J - eta_t, kt H): the tests boost that vector to the lab frame and
+compare.  This scheme keeps kt_1 = 0.
 
 Test infrastructure only: tests, smoke() and the bench's CPU baseline may use
 this module; the library never does.
@@ -41,11 +48,11 @@ def comoving(E, F, P, v):
 
 
 def four_force(E, F, P, v, kt_a, kt_0, eta_t, kt_1=0.0):
-    """(S_0, S [3, ...]) of step 4 of the coupling (and J, H, H_0)."""
+    """(S_0, S [3, ...]) of step 4 of the coupling (and J, H, H^0)."""
     J, H = comoving(E, F, P, v)
     W = lorentz(v)
     kt = kt_a + (kt_0 - kt_1 / 3.0)
-    H0 = -np.einsum("i...,i...->...", v, H)
+    H0 = np.einsum("i...,i...->...", v, H)  # time component of H^mu (H^mu u_mu = 0)
     emit = W * (kt_a * J - eta_t)
     S0 = emit + kt * H0
     S = emit[None] * v + kt * H

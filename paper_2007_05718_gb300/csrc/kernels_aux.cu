@@ -382,10 +382,12 @@ __global__ void k_total_partials16(Grid g, int N, const ST* __restrict__ pop,
 // Coupling outputs (Sec. 5, coupling step 4): from the site's E, F, P and
 // the fluid velocity v, the comoving J = W^2 (E - 2 F.v + P:vv) (Eq. J),
 // H_j = W^3 (F.v - E) v_j + W h_ji F^i - W h_ji v_k P^ik with
-// h_ij = W^2 v_i v_j + delta_ij, H_0 = -v.H (from H_mu u^mu = 0, signature
-// -+++), and S_0 = W (kt_a J - eta_t) + kt H_0, S_j = W (kt_a J - eta_t) v_j +
-// kt H_j with kt = kt_a + kt_0 (kt_1 = 0).  ST = float: populations; 16-bit
-// types: the deviation form against the E array `e`.
+// h_ij = W^2 v_i v_j + delta_ij, and S_0 = W (kt_a J - eta_t) + kt H^0,
+// S_j = W (kt_a J - eta_t) v_j + kt H_j with kt = kt_a + kt_0 (kt_1 = 0):
+// the lab components of the four-vector (kt_a J - eta_t) u^mu + kt H^mu, with
+// H^0 = v.H the time component of the comoving flux (H^mu u_mu = 0,
+// signature -+++).  ST = float: populations; 16-bit types: the deviation
+// form against the E array `e`.
 template <class ST>
 __global__ void k_coupling(Grid g, int N, const ST* __restrict__ pop, const float* __restrict__ e,
                            DirTable t, MovingCoef c, float* __restrict__ Jo, float* __restrict__ Ho,
@@ -441,7 +443,8 @@ __global__ void k_coupling(Grid g, int N, const ST* __restrict__ pop, const floa
     const float kta = c.kta ? c.kta[s] : c.kta_s, kt0 = c.kt0 ? c.kt0[s] : c.kt0_s;
     const float etat = c.etat ? c.etat[s] : c.etat_s;
     const float kt = kta + kt0;
-    const float H0 = -(vx * Hx + vy * Hy + vz * Hz);
+    // time component of the comoving flux four-vector, H^mu u_mu = 0
+    const float H0 = vx * Hx + vy * Hy + vz * Hz;
     const float emit = W * (kta * J - etat);
     So[s] = fmaf(kt, H0, emit);
     So[g.sites + s] = fmaf(kt, Hx, emit * vx);

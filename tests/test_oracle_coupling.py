@@ -57,5 +57,44 @@ def test_H0_makes_H_orthogonal_to_u_and_sources_in_equilibrium_vanish():
     E, F, P = _lab_moments(J, H, v)
     S0, S, Jc, Hc, H0 = CP.four_force(np.array([E]), F[:, None], P[:, :, None], v[:, None],
                                       kt_a=1.0, kt_0=0.0, eta_t=0.0)
+    # H^mu u_mu = -W H^0 + W v.H = 0
     W = 1.0 / np.sqrt(1.0 - v @ v)
-    assert abs(W * H0[0] + W * (v @ Hc[:, 0])) < 1e-12
+    assert abs(-W * H0[0] + W * (v @ Hc[:, 0])) < 1e-12
+
+
+def _boost(v):
+    """Lorentz boost Lambda(v): rest-frame components of a four-vector ->
+    components in the lab frame in which the rest frame moves with v."""
+    W = 1.0 / np.sqrt(1.0 - v @ v)
+    L = np.eye(4)
+    L[0, 0] = W
+    L[0, 1:] = L[1:, 0] = W * v
+    L[1:, 1:] += (W - 1.0) * np.outer(v, v) / (v @ v)
+    return L
+
+
+def test_four_force_is_the_boosted_rest_frame_source():
+    """In the fluid rest frame the source four-vector is (kt_a J - eta_t,
+    kt H): the energy exchange and the momentum drag of Sec. 5.  Boosted to
+    the lab frame it must equal (S_0, S_j) of the oracle, out of equilibrium
+    (kt_a J != eta_t), with a comoving flux H != 0 and v != 0, so that the
+    W (kt_a J - eta_t) v_j term and the kt H_0 term both carry weight: a sign
+    slip in either fails here."""
+    g = np.random.default_rng(9)
+    for _ in range(50):
+        v = g.normal(size=3)
+        v *= g.uniform(0.05, 0.9) / np.linalg.norm(v)
+        J = g.uniform(0.1, 5.0)
+        Hr = g.normal(size=3) * 0.3 * J             # rest-frame comoving flux
+        kt_a, kt_0 = g.uniform(0.1, 10.0), g.uniform(0.0, 10.0)
+        eta_t = kt_a * J * g.uniform(0.2, 3.0)      # away from equilibrium
+        L = _boost(v)
+        Hlab = L @ np.concatenate([[0.0], Hr])      # comoving flux four-vector in the lab
+        E, F, P = _lab_moments(J, Hlab[1:], v)
+        G = L @ np.concatenate([[kt_a * J - eta_t], (kt_a + kt_0) * Hr])
+        S0, S, Jc, Hc, H0 = CP.four_force(np.array([E]), F[:, None], P[:, :, None], v[:, None],
+                                          kt_a=kt_a, kt_0=kt_0, eta_t=eta_t)
+        scale = abs(kt_a * J - eta_t) + (kt_a + kt_0) * np.linalg.norm(Hr)
+        assert abs(S0[0] - G[0]) < 1e-11 * scale
+        assert np.allclose(S[:, 0], G[1:], rtol=0, atol=1e-11 * scale)
+        assert abs(H0[0] - Hlab[0]) < 1e-11 * J
