@@ -17,6 +17,7 @@ struct lb_rt {
   int N = 0;                    // directions, external (user) order
   int Ni = 0;                   // internal directions including inert padding
   int dpt = 0, zc = 0;          // tile plan of the static kernel
+  bool pipelined = false;       // single-problem static steps run the pipelined kernel
   int nzc = 0, ctas = 0;        // its persistent grid: z chunks, CTAs
   std::vector<int> ext_of_int;  // internal -> external index (-1: padding)
   std::vector<int> int_of_ext;  // external -> internal index

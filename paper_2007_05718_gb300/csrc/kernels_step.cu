@@ -250,6 +250,7 @@ cudaError_t launch_moving(const StepLaunch& L, const MovingCoef& c, const DirTab
 
 cudaError_t launch_step_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                                int storage, cudaStream_t s, int* nblocks) {
+  if (L.sc) return launch_sc_static(L, c, t, storage, s, nblocks);
   if (storage != ST_F32) return launch_tma16_static(L, c, t, storage, s, nblocks);
   return launch_tma_static(L, c, t, L.dpt, L.zc, s, nblocks);
 }

@@ -641,7 +641,8 @@ constexpr int kRing = 2;
   X(10, 1, 544, 96)        \
   X(8, 2, 512, 128)        \
   X(4, 2, 512, 128)        \
-  X(4, 1, 640, 96)
+  X(4, 1, 640, 96)         \
+  X(5, 1, 320, 96)
 
 }  // namespace
 
@@ -692,11 +693,13 @@ cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const Di
 // tile loads zlen + 1 planes rounded up to whole batches, plus a small
 // per-tile overhead).
 cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage, int* nzc,
-                             int* ctas, bool moving) {
+                             int* ctas, bool moving, bool sc) {
   const int G = Ni / dpt;
   int per_sm = 0;
   cudaError_t e = cudaErrorInvalidValue;
-  if (moving) {
+  if (sc) {
+    e = occupancy_sc(storage, dpt, zc, G, &per_sm);
+  } else if (moving) {
     e = storage == ST_F32 ? occupancy_tma_moving(dpt, G, &per_sm)
                           : occupancy_tma16_moving(storage, dpt, G, &per_sm);
   } else if (storage == ST_F32) {

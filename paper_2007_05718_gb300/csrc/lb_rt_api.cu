@@ -108,31 +108,67 @@ void plan_directions(lb_rt* h) {
     // the first plan (in the kernel's order of preference) that fits and
     // pads the direction set by at most 4 % more than the tightest plan
     // (a moving fluid with no fitting plan falls back to the one-thread-per-
-    // site kernel with this ordering and no padding)
+    // site kernel with this ordering and no padding).  A static handle
+    // prefers the pipelined kernel's plans; the plan it takes must also fit
+    // the first-generation kernel, which runs the batched launches (the
+    // direction grouping fixes the summation order, so a problem gives the
+    // same bits on both).
     const bool f32 = h->cfg.storage == LB_RT_F32;
     const bool mov = h->cfg.moving != 0;
-    const int (*plans)[3] = mov ? kTilePlansMoving : f32 ? kTilePlans : kTilePlans16;
-    const int nplans = mov ? kNumTilePlansMoving : f32 ? kNumTilePlans : kNumTilePlans16;
-    std::vector<int> ni_of(nplans, -1);
-    int min_ni = 1 << 30;
-    for (int p = 0; p < nplans; ++p) {
-      const int dpt = plans[p][0], zc = plans[p][1];
-      if (zc > 1 && zc > h->grid.nz) continue;
+    const int (*old_plans)[3] = mov ? kTilePlansMoving : f32 ? kTilePlans : kTilePlans16;
+    const int n_old = mov ? kNumTilePlansMoving : f32 ? kNumTilePlans : kNumTilePlans16;
+    auto pad_ni = [&](int dpt) {
       int ni = 0;
       for (auto& c : cls) ni += (int)(c.size() + dpt - 1) / dpt * dpt;
-      const int warps = ni / dpt;
-      if (ni > kMaxInternalDirs || 32 * warps > plans[p][2]) continue;
-      const size_t smem = mov ? step_tile_smem_moving(dpt, warps)
-                          : f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
-      if (smem > 226 * 1024) continue;
-      ni_of[p] = ni;
-      min_ni = std::min(min_ni, ni);
-    }
+      return ni;
+    };
+    auto old_fits = [&](int dpt, int zc) {
+      for (int p = 0; p < n_old; ++p) {
+        if (old_plans[p][0] != dpt || old_plans[p][1] != zc) continue;
+        if (zc > 1 && zc > h->grid.nz) return false;
+        const int ni = pad_ni(dpt), warps = ni / dpt;
+        if (ni > kMaxInternalDirs || 32 * warps > old_plans[p][2]) return false;
+        const size_t smem = mov ? step_tile_smem_moving(dpt, warps)
+                            : f32 ? step_tile_smem(dpt, zc, warps) : step_tile_smem16(dpt, zc, warps);
+        return smem <= 226 * 1024;
+      }
+      return false;
+    };
+    auto choose = [&](const int (*plans)[3], int nplans, bool sc) {
+      std::vector<int> ni_of(nplans, -1);
+      int min_ni = 1 << 30;
+      for (int p = 0; p < nplans; ++p) {
+        const int dpt = plans[p][0], zc = plans[p][1];
+        if (!old_fits(dpt, zc)) continue;
+        const int ni = pad_ni(dpt), warps = ni / dpt;
+        if (sc && (32 * (warps + zc) > plans[p][2] ||
+                   step_tile_smem_sc(h->cfg.storage, dpt, zc, warps) > 226 * 1024))
+          continue;
+        ni_of[p] = ni;
+        min_ni = std::min(min_ni, ni);
+      }
+      for (int p = 0; p < nplans; ++p)
+        if (ni_of[p] >= 0 && ni_of[p] * 100 <= min_ni * 104) return p;
+      return -1;
+    };
     int best = -1;
-    for (int p = 0; p < nplans && best < 0; ++p)
-      if (ni_of[p] >= 0 && ni_of[p] * 100 <= min_ni * 104) best = p;
-    h->dpt = best >= 0 ? plans[best][0] : 0;
-    h->zc = best >= 0 ? plans[best][1] : 0;
+    h->pipelined = false;
+    // float32 populations keep the first-generation kernel, which measured
+    // faster on the 42- and 162-direction workloads; 16-bit storage takes the
+    // pipelined one
+    if (!mov && !f32) {
+      best = choose(kTilePlansSC, kNumTilePlansSC, true);
+      if (best >= 0) {
+        h->pipelined = true;
+        h->dpt = kTilePlansSC[best][0];
+        h->zc = kTilePlansSC[best][1];
+      }
+    }
+    if (best < 0) {
+      best = choose(old_plans, n_old, false);
+      h->dpt = best >= 0 ? old_plans[best][0] : 0;
+      h->zc = best >= 0 ? old_plans[best][1] : 0;
+    }
     for (auto& c : cls) {
       for (int e : c) h->ext_of_int.push_back(e);
       if (h->dpt)
@@ -219,6 +255,7 @@ lb_rt_status run_steps(lb_rt* h, int nsteps, float* mE, float* mF) {
     L.e_in = h->ef[h->cur];
     L.e_out = h->ef[h->cur ^ 1];
     L.err = h->err;
+    L.sc = h->pipelined;
     L.budget_partials = nullptr;
     L.partials_cap = h->partials_cap;
     if (s == nsteps - 1) {
@@ -440,7 +477,15 @@ lb_rt_status lb_rt_create(const lb_rt_config* cfg, lb_rt** out) {
     }
     h->tmap_ok = true;
     e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, cfg->storage, &h->nzc, &h->ctas,
-                         cfg->moving != 0);
+                         cfg->moving != 0, h->pipelined);
+    if (e != cudaSuccess && h->pipelined) {
+      // the pipelined kernel cannot be resident with this plan on this
+      // device: the first-generation kernel runs the same plan
+      (void)cudaGetLastError();
+      h->pipelined = false;
+      e = plan_static_grid(h->grid, h->Ni, h->dpt, h->zc, cfg->storage, &h->nzc, &h->ctas,
+                           cfg->moving != 0, false);
+    }
     if (e != cudaSuccess) {
       g_create_msg = std::string("static kernel grid: ") + cudaGetErrorString(e);
       lb_rt_destroy(h);

@@ -94,6 +94,7 @@ struct StepLaunch {
   unsigned* err;            // device error word
   float* mom_E;             // FP32 static step: E of the new state, dense [sites], or nullptr
   float* mom_F;             // FP32 static step: F of the new state, dense [3][sites], or nullptr
+  bool sc;                  // static step: the pipelined kernel (kernels_sc.cu)
 };
 
 // One problem of a static step launch.  The single-problem launch passes it
@@ -172,7 +173,7 @@ size_t step_tile_smem(int dpt, int zc, int warps);
 // z chunks and CTA count of the static kernel's persistent grid for this
 // grid and plan on the current device (occupancy query).
 cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage, int* nzc,
-                             int* ctas, bool moving = false);
+                             int* ctas, bool moving = false, bool sc = false);
 // Moving fluid, FP32 populations, TMA tiles (kernels_tma_moving.cu): one
 // plane per batch; plans (directions per warp, 1, thread cap).
 extern const int kTilePlansMoving[][3];
@@ -184,6 +185,16 @@ cudaError_t launch_tma_moving(const StepLaunch& L, const MovingCoef& c, const Di
 cudaError_t occupancy_tma16_moving(int storage, int dpt, int G, int* per_sm);
 cudaError_t launch_tma16_moving(const StepLaunch& L, const MovingCoef& c, const DirTable& t,
                                 int storage, cudaStream_t s, int* nblocks);
+// Pipelined static step (kernels_sc.cu), float32 and 16-bit storage, single
+// problem: plans (directions per warp, planes per batch, thread cap with the
+// coefficient warps); shared memory and resident CTAs per SM for
+// `stream_warps` stream warps.
+extern const int kTilePlansSC[][3];
+extern const int kNumTilePlansSC;
+size_t step_tile_smem_sc(int storage, int dpt, int zc, int stream_warps);
+cudaError_t occupancy_sc(int storage, int dpt, int zc, int stream_warps, int* per_sm);
+cudaError_t launch_sc_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t, int storage,
+                             cudaStream_t s, int* nblocks);
 // 16-bit storage (kernels_tma16.cu): f_i = I_i / w_i = E (1 + q_i) with E a
 // padded float32 [PZ][PY][PX] array and q_i stored in FP16 or BF16.
 size_t step_tile_smem16(int dpt, int zc, int warps);

@@ -50,3 +50,49 @@ def test_moving_uniform_scalars_and_no_velocity(cuda):
     I, E, F, P, b = gpu_run(p, 4)
     Io, Eo, *_ = oracle_run(p, 4)
     assert rel_l2(I, Io) <= TOL_F32
+
+
+@pytest.mark.parametrize("storage,tol", [(lbrt.LB_RT_F32, TOL_F32), (lbrt.LB_RT_F16_DEV, 2e-3)])
+def test_moving_large_direction_set_site_kernel(cuda, storage, tol):
+    """192 Gauss-Legendre directions (12 in mu x 16 in phi, four upwind
+    classes of 48) fit none of the tile plans of the moving kernels (at most
+    176 internal directions), so the step runs on the one-thread-per-site
+    kernel; it must match the oracle like the tiled kernels do."""
+    shape = (6, 7, 9)
+    v = 0.5 * np.stack([W.smooth_field(shape, 81 + k) for k in range(3)]).astype(np.float32) / 3.0
+    p = Problem(3, shape, "gl", gl=(12, 16), bc="pvp", storage=storage,
+                moving=dict(v=v, kt_a=W.random_fields(shape, 85, 0.0, 10.0),
+                            kt_0=W.random_fields(shape, 86, 0.0, 20.0), eta_t=1.0),
+                state_kind=lbrt.LB_RT_STATE_ISOTROPIC,
+                state=(1.0 + 0.5 * W.smooth_field(shape, 87)).astype(np.float32))
+    I, E, F, P, b = gpu_run(p, 6)
+    Io, Eo, Fo, Po, bo, lat = oracle_run(p, 6)
+    assert rel_l2(E, Eo) <= tol
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Eo) <= tol
+
+
+@pytest.fixture(scope="module")
+def c5_48():
+    """The moving-fluid configuration's generator on 48^3 (ico-162, periodic),
+    a seeded P1 start, and the oracle's 10 steps of it (computed once)."""
+    n, steps = 48, 10
+    mf = W.moving_fluid(n)
+    E0, F0 = W.random_moments((n, n, n), 49)
+    mov = dict(v=mf["v"], kt_a=mf["kt_a"], kt_0=mf["kt_0"], eta_t=mf["eta_t"])
+    state = np.concatenate([E0[None], F0]).astype(np.float32)
+    p = Problem(3, (n, n, n), "ico", level=2, moving=mov, state_kind=lbrt.LB_RT_STATE_P1, state=state)
+    Io, Eo, Fo, Po, bo, lat = oracle_run(p, steps)
+    return dict(mov=mov, state=state, steps=steps, Eo=Eo, Fo=Fo, n=n)
+
+
+@pytest.mark.parametrize("storage,tol", [(lbrt.LB_RT_F32, TOL_F32), (lbrt.LB_RT_F16_DEV, 2e-3)])
+def test_c5_48_cubed_ten_steps(cuda, c5_48, storage, tol):
+    """Ten mixed-frame steps (App. B) of the 48^3 instance of the moving-fluid
+    configuration against the FP64 oracle: E and F within 1e-5 (FP32
+    populations) or 2e-3 (FP16)."""
+    n = c5_48["n"]
+    p = Problem(3, (n, n, n), "ico", level=2, storage=storage, moving=c5_48["mov"],
+                state_kind=lbrt.LB_RT_STATE_P1, state=c5_48["state"])
+    I, E, F, P, b = gpu_run(p, c5_48["steps"])
+    assert rel_l2(E, c5_48["Eo"]) <= tol
+    assert np.linalg.norm(F - c5_48["Fo"]) / np.linalg.norm(c5_48["Eo"]) <= tol

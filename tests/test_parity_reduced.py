@@ -26,19 +26,31 @@ def _check(p, steps, f_scale="F", tol_f=TOL_16):
     return E, F, b, Eo, bo, eE, eF
 
 
-@pytest.mark.parametrize("storage", STORAGES)
-def test_sphere_reduced(cuda, storage):
-    """Radiating sphere (kappa_a R = 10), 32^3, 42 directions, vacuum faces, 150 steps."""
+def test_sphere_reduced(cuda):
+    """Radiating sphere (kappa_a R = 10), 32^3, 42 directions, vacuum faces,
+    150 steps, FP16 storage.  Outside the sphere the field streams freely and
+    is strongly beamed, so the deviations from isotropy are of order one.
+    BF16 (8 significant bits) is not validated in this regime (its flux error
+    here is about 5e-3; the header says to use FP16 for it) and is tested on
+    the near-isotropic problems below, at the same 2e-3 bar."""
     sp = W.radiating_sphere(32, 10.0)
-    p = Problem(3, (32, 32, 32), "ico", level=1, bc="vvv", storage=storage,
+    p = Problem(3, (32, 32, 32), "ico", level=1, bc="vvv", storage=lbrt.LB_RT_F16_DEV,
                 coef=dict(kappa_a=sp["kappa_a"], eta=sp["eta"]),
                 state_kind=lbrt.LB_RT_STATE_ISOTROPIC, state=sp["E0"], budget=True)
-    # Outside the sphere the field streams freely and is strongly beamed, so
-    # the deviations from isotropy are of order one; BF16 keeps 8 significant
-    # bits (rounding 2^-9 of the deviation per step) and its flux error here
-    # is 4.9e-3 after 150 steps, while E stays within 2e-3.  FP16 (11 bits)
-    # meets 2e-3 on both.
-    _check(p, 150, tol_f=TOL_16 if storage == lbrt.LB_RT_F16_DEV else 6e-3)
+    _check(p, 150)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_thick_sphere_with_scattering_reduced(cuda, storage):
+    """A scattering-dominated sphere: kappa_a R = 10 inside with kappa_0 = 400
+    /L everywhere, so the field stays near isotropy and both 16-bit formats
+    are in their validated regime; 32^3, 42 directions, vacuum faces, 150
+    steps, E and F at 2e-3."""
+    sp = W.radiating_sphere(32, 10.0)
+    p = Problem(3, (32, 32, 32), "ico", level=1, bc="vvv", storage=storage,
+                coef=dict(kappa_a=sp["kappa_a"], kappa_0=400.0, eta=sp["eta"]),
+                state_kind=lbrt.LB_RT_STATE_ISOTROPIC, state=sp["E0"], budget=True)
+    _check(p, 150)
 
 
 @pytest.mark.parametrize("storage", STORAGES)
