@@ -1,17 +1,23 @@
 #!/usr/bin/env python3
-"""Benchmark: one timestep of the grey radiative LB scheme (stream + exact
-implicit collision) on the radiating-sphere workload, 128^3 sites x 42
-directions (icosahedral geodesic level 1), float32 populations, vacuum
-faces, kappa_a = eta = 40 inside R = 0.25 (kappa_a R = 10), cfl 0.5.
+"""Benchmark of the grey radiative LB step (fused pull-stream + exact implicit
+collision, Sec. 3.3) on its largest single-GPU configuration: optically thick
+diffusion, 256^3 periodic sites x 162 directions (icosahedral geodesic level
+2), pure isotropic scattering kappa_0 = 1e3 /L (kappa_0 dx = 3.9), Gaussian
+initial E (sigma 8 cells) with isotropic populations, cfl 0.5.
 
-Prints one JSON line.  `value` is site-direction updates per second over
-the timed steps (inputs resident in HBM, 705 MB of populations per step,
-larger than L2); `e2e` is the same metric through the C ABI with host
-buffers: every step hands new fluid coefficients (kappa_a, eta) over in
-pinned host memory (lb_rt_set_fluid with LB_RT_HOST_MAPPED: the step kernel
-reads them across the host link), steps, and returns E and F to pinned host
-memory (lb_rt_step_moments: the collision epilogue writes them across the
-host link), as a coupled hydrodynamics code does each step.
+Prints one JSON line.  The headline `value` is site-direction updates per
+second of the float32-population step over the timed steps (inputs resident
+in HBM: 22 GB of populations per step, far larger than L2).  Sub-lines, each
+with its own roofline: the same configuration with FP16 and BF16
+equilibrium-deviation storage (the storage the configuration names; float32
+arithmetic), the radiating sphere 128^3 x 42 (FP32 and FP16) and the moving
+background fluid 256^3 x 162 (App. B; FP32 and FP16).  `e2e` is the headline
+metric through the C ABI with host buffers: every step hands a per-site
+scattering opacity over in pinned host memory (lb_rt_set_fluid with
+LB_RT_HOST_MAPPED, read in place by the step kernel), steps, and returns E
+and F to pinned host memory (lb_rt_step_moments), as a coupled fluid code
+does each step.  The FP64 oracle is timed on the host cores beside it, with
+one thread and with every core.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -19,7 +25,6 @@ N > 1 (torchrun) runs independent replicas, one per GPU (weak scaling).
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -30,14 +35,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_SIDE = 128
-LEVEL = 1
-NDIR = 42
-KAPPA_R = 10.0
+N_SIDE = 256
+LEVEL = 2
+KAPPA0_DX = 3.90625          # kappa_0 dx of the diffusion configuration (kappa_0 = 1e3 /L at 256^3)
+SIGMA_CELLS = 8.0
 CFL = 0.5
 METRIC = "site-direction updates/s"
 UNIT = "sd/s"
-WORKLOAD = "3D radiating sphere 128^3 x 42 dirs (icosahedral L1), FP32 populations, kappa_a R = 10, vacuum faces, cfl 0.5"
+WORKLOAD = ("3D optically thick diffusion 256^3 x 162 dirs (icosahedral L2), periodic, pure "
+            "scattering kappa_0 = 1e3 /L, Gaussian E0 (sigma 8 cells), cfl 0.5")
 
 
 def _peaks():
@@ -53,35 +59,55 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-PROFILE = os.path.join(ROOT, "profiles", "step_static_f32_sphere128_42.md")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2007_05718_gb300", "csrc", f)
-                  for f in ("kernels_tma.cu", "tma_common.cuh")]
+CSRC = os.path.join(ROOT, "paper_2007_05718_gb300", "csrc")
+# the ncu summary of each timed kernel (traffic per launch, scaled to the
+# bench size where the summary says so) and the sources it was captured from
+PROFILES = {
+    "c3_fp32": ("step_static_f32_diffusion256_162.md", ("kernels_tma.cu", "tma_common.cuh")),
+    "c3_fp16": ("step_static_f16_diffusion256_162.md", ("kernels_sc.cu", "tma_common.cuh")),
+    "c2_fp32": ("step_static_f32_sphere128_42.md", ("kernels_tma.cu", "tma_common.cuh")),
+    "c2_fp16": ("step_static_f16_sphere128_42.md", ("kernels_sc.cu", "tma_common.cuh")),
+    "c5_fp32": ("step_moving_f32_shear128_162.md", ("kernels_tma_moving.cu", "tma_common.cuh")),
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(f, "rb").read())
+    for f in files:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profiles():
-    """Per-launch DRAM bytes of the step kernel from the committed ncu
-    summary, or None when the kernel source changed after the capture."""
-    if not os.path.exists(PROFILE):
+def _traffic(key):
+    """DRAM bytes per launch of a line's kernel from its committed ncu
+    summary, or None when there is none or the kernel source changed after
+    the capture."""
+    if key not in PROFILES:
+        return None
+    name, files = PROFILES[key]
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(PROFILE):
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16")):
-            k, v = line.strip().split(":", 1)
+    for line in open(path):
+        s = line.strip()
+        if s.startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16")) and ":" in s:
+            k, v = s.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash(files):
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def roofline(key, bytes_per_launch, ms_per_launch):
+    peak, kind = _peaks()
+    achieved = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic(key), "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_per_launch}
 
 
 class Clocks:
@@ -98,7 +124,7 @@ class Clocks:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -113,12 +139,12 @@ class Clocks:
                 if n > 0:
                     self.skip = n
                     break
-                time.sleep(0.02)
+                time.sleep(0.01)
 
     def stop(self):
         if not self.proc:
             return None
-        time.sleep(0.06)  # one more sample interval
+        time.sleep(0.03)  # one more sample interval
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -178,66 +204,198 @@ def aggregate_rate(units_per_step_per_rank, ws, ms_max, steps):
     return units_per_step_per_rank * ws * steps / (ms_max * 1e-3)
 
 
-def _workload_fields():
-    from paper_2007_05718_gb300 import workloads as W
-    return W.radiating_sphere(N_SIDE, KAPPA_R)
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host cores (the reference arm and the CPU baseline)
+# ---------------------------------------------------------------------------
 
-
-def oracle_sample_time(n_side, steps=1):
-    """Time the FP64 oracle (as it stands) on an n_side^3 sub-box of the same
-    workload, single thread; returns (seconds per step, sd per step)."""
-    code = r"""
-import os, sys, time, json
-sys.path.insert(0, %r)
+ORACLE_CODE = r"""
+import sys, time, json
+sys.path.insert(0, %(root)r)
 import numpy as np
 from oracle import directions as D, lb
 from paper_2007_05718_gb300 import workloads as W
-n = %d
-sp = W.radiating_sphere(n, %r)
-nv, w = D.icosphere(%d)
-lat = lb.Lattice(3, (n, n, n), nv, w, cfl=%r, dx=1.0 / n, bc=(lb.VACUUM,) * 3)
-co = lb.Static(kappa_a=sp["kappa_a"].astype(float), eta=sp["eta"].astype(float))
-I = lb.isotropic(sp["E0"].astype(float), lat)
+n, steps = %(n)d, %(steps)d
+nv, w = D.icosphere(%(level)d)
+lat = lb.Lattice(3, (n, n, n), nv, w, cfl=%(cfl)r, dx=1.0 / n, bc=(lb.PERIODIC,) * 3)
+co = lb.Static(kappa_0=%(k0dx)r * n)
+I = lb.isotropic(W.gaussian_E0((n, n, n), %(sigma)r).astype(float), lat)
+I = lb.step(I, lat, co)
 t0 = time.perf_counter()
-for _ in range(%d):
+for _ in range(steps):
     I = lb.step(I, lat, co)
 dt = time.perf_counter() - t0
-print(json.dumps({"sec": dt / %d, "sd": n ** 3 * len(w)}))
-""" % (ROOT, n_side, KAPPA_R, LEVEL, CFL, steps, steps)
+print(json.dumps({"sec": dt, "sd": n ** 3 * len(w) * steps}))
+"""
+
+
+def oracle_time(n_side, steps, procs):
+    """Run `procs` copies of the FP64 oracle (numpy as it stands, one thread
+    each) at once, each on an n_side^3 periodic sub-box of the diffusion
+    configuration (same kappa_0 dx, sigma and cfl), each in a fresh
+    interpreter; returns (aggregate sd/s, seconds of the slowest copy)."""
+    code = ORACLE_CODE % dict(root=ROOT, n=n_side, steps=steps, level=LEVEL, cfl=CFL, k0dx=KAPPA0_DX,
+                              sigma=SIGMA_CELLS * n_side / N_SIDE if n_side < 64 else SIGMA_CELLS)
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["sec"], d["sd"]
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    sd, sec = 0.0, 0.0
+    for p in ps:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError("oracle timing failed: " + err[-2000:])
+        d = json.loads(out.strip().splitlines()[-1])
+        sd += d["sd"]
+        sec = max(sec, d["sec"])
+    return sd / sec, sec
+
+
+def cpu_baselines(n_side=48, steps=6):
+    cores = len(os.sched_getaffinity(0))
+    one, t1 = oracle_time(n_side, steps, 1)
+    allc, tall = oracle_time(n_side, steps, cores)
+    sample = ("%d oracle steps (FP64 numpy) of a %d^3 periodic sub-box of the diffusion configuration "
+              "(162 dirs, same kappa_0 dx and cfl)" % (steps, n_side))
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample + ", one copy per core at once; seconds %.1f" % tall,
+            "one_thread": {"value": one, "unit": UNIT, "cores": 1, "sample": sample + ", seconds %.1f" % t1}}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    n_sample = 48
-    for _ in range(max(args.warmup, 0) and 1):
-        oracle_sample_time(16, 1)
-    sec, sd = oracle_sample_time(n_sample, max(args.steps, 1))
-    value = sd / sec
-    ncores = len(os.sched_getaffinity(0))
-    sample = "%d^3 sub-box of the same workload (42 dirs), %d oracle steps, FP64 numpy, 1 thread" % (
-        n_sample, args.steps)
+    cores = len(os.sched_getaffinity(0))
+    n_sample = 40
+    oracle_time(16, 1, 1)  # warm-up of the interpreter and numpy
+    vals = []
+    for _ in range(max(args.steps, 1) if args.steps <= 3 else 3):
+        v, sec = oracle_time(n_sample, 2, cores)
+        vals.append((v, sec))
+    value = statistics.median(v for v, _ in vals)
+    sec = statistics.median(s for _, s in vals)
+    sample = ("%d^3 periodic sub-box of the diffusion configuration (162 dirs), 2 oracle steps per "
+              "copy, one FP64 numpy copy per host core (%d) at once" % (n_sample, cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (N_SIDE ** 3 * 162) / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sites": N_SIDE ** 3, "ndir": NDIR},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample, "host_cores": ncores},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sites": N_SIDE ** 3, "ndir": 162},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample + "; seconds per copy %.1f" % sec},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU lines
+# ---------------------------------------------------------------------------
+
+def _time_steps(lbrt, h, stream, steps):
+    """CUDA-event time (ms) of `steps` single-step launches on the handle's stream."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        lbrt.lb_rt_step(h, 1)
+    b.record(stream)
+    b.synchronize()
+    lbrt.lb_rt_sync(h)
+    return a.elapsed_time(b), None
+
+
+def diffusion_line(key, storage, steps, warmup, n=N_SIDE):
+    """The diffusion configuration with the given storage: ms per step and its roofline."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    E0 = torch.from_numpy(W.gaussian_E0((n, n, n), SIGMA_CELLS)).cuda()
+    h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL, cfl=CFL, dx=1.0 / n,
+                          bc=(lbrt.LB_RT_PERIODIC,) * 3, storage=storage, stream=stream.cuda_stream)
+    try:
+        lbrt.lb_rt_set_fluid(h, kappa_0=KAPPA0_DX * n)
+        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        lbrt.lb_rt_step(h, warmup)
+        ms, _ = _time_steps(lbrt, h, stream, steps)
+    finally:
+        lbrt.lb_rt_destroy(h)
+        torch.cuda.empty_cache()
+    ms /= steps
+    sites = n ** 3
+    per_sd = 8.0 if storage == lbrt.LB_RT_F32 else 4.0
+    per_site = 0.0 if storage == lbrt.LB_RT_F32 else 8.0   # E read + written (16-bit storage)
+    nbytes = sites * (N * per_sd + per_site)
+    return {"ms_per_step": ms, "value": sites * N / (ms * 1e-3), "unit": UNIT,
+            "roofline": roofline(key, nbytes, ms)}
+
+
+def sphere_line(key, storage, steps, warmup, n=128, kappa_r=10.0):
+    """Radiating sphere 128^3 x 42 (vacuum faces, kappa_a R = 10): ms per step and roofline."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    sp = W.radiating_sphere(n, kappa_r)
+    stream = torch.cuda.Stream()
+    h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=1, cfl=CFL, dx=1.0 / n,
+                          bc=(lbrt.LB_RT_VACUUM,) * 3, storage=storage, stream=stream.cuda_stream)
+    try:
+        lbrt.lb_rt_set_fluid(h, kappa_a=torch.from_numpy(sp["kappa_a"]).cuda(),
+                             eta=torch.from_numpy(sp["eta"]).cuda())
+        lbrt.lb_rt_set_state(h, torch.from_numpy(sp["E0"]).cuda(), lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        lbrt.lb_rt_step(h, warmup)
+        ms, _ = _time_steps(lbrt, h, stream, steps)
+    finally:
+        lbrt.lb_rt_destroy(h)
+        torch.cuda.empty_cache()
+    ms /= steps
+    sites = n ** 3
+    per_sd = 8.0 if storage == lbrt.LB_RT_F32 else 4.0
+    per_site = 8.0 if storage == lbrt.LB_RT_F32 else 16.0   # kappa_a, eta (+ E r/w in 16-bit)
+    nbytes = sites * (N * per_sd + per_site)
+    return {"ms_per_step": ms, "value": sites * N / (ms * 1e-3), "unit": UNIT,
+            "roofline": roofline(key, nbytes, ms),
+            "workload": "radiating sphere 128^3 x 42, vacuum faces, kappa_a R = 10"}
+
+
+def moving_line(key, storage, steps, warmup, n=256, level=2):
+    """Moving background fluid (App. B), 256^3 x 162 periodic, the seeded
+    shear flow: ms per step and roofline."""
+    import torch
+    from paper_2007_05718_gb300 import lbrt
+    from paper_2007_05718_gb300 import workloads as W
+    mf = W.moving_fluid(n)
+    fields = {k: torch.from_numpy(mf[k]).cuda() for k in ("v", "kt_a", "kt_0", "eta_t")}
+    stream = torch.cuda.Stream()
+    h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=level, cfl=CFL,
+                          moving=True, storage=storage, stream=stream.cuda_stream)
+    try:
+        lbrt.lb_rt_set_fluid(h, **fields)
+        lbrt.lb_rt_set_state(h, torch.ones((n, n, n), dtype=torch.float32, device="cuda"),
+                             lbrt.LB_RT_STATE_ISOTROPIC)
+        N = lbrt.lb_rt_directions(h)[0].shape[0]
+        lbrt.lb_rt_step(h, warmup)
+        ms, _ = _time_steps(lbrt, h, stream, steps)
+    finally:
+        lbrt.lb_rt_destroy(h)
+        del fields
+        torch.cuda.empty_cache()
+    ms /= steps
+    sites = n ** 3
+    per_sd = 8.0 if storage == lbrt.LB_RT_F32 else 4.0
+    per_site = 24.0 if storage == lbrt.LB_RT_F32 else 32.0   # v, kt_a, kt_0, eta_t (+ E r/w)
+    nbytes = sites * (N * per_sd + per_site)
+    return {"ms_per_step": ms, "value": sites * N / (ms * 1e-3), "unit": UNIT,
+            "roofline": roofline(key, nbytes, ms),
+            "workload": "moving fluid 256^3 x 162 periodic shear flow (|v| <= 0.6), density-scaled opacities"}
 
 
 def collision_mode_costs(steps=20, warmup=3, n=128):
@@ -259,13 +417,8 @@ def collision_mode_costs(steps=20, warmup=3, n=128):
         lbrt.lb_rt_set_fluid(h, kappa_a=1.0, kappa_0=1000.0, lam=0.5, eta=1.0)
         lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
         lbrt.lb_rt_step(h, warmup)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lbrt.lb_rt_step(h, steps)
-        b.record(stream)
-        b.synchronize()
-        out[name + "_ms"] = a.elapsed_time(b) / steps
+        ms, _ = _time_steps(lbrt, h, stream, steps)
+        out[name + "_ms"] = ms / steps
         lbrt.lb_rt_destroy(h)
     out["implicit_over_explicit"] = out["implicit_exact_ms"] / out["explicit_ms"]
     out["lambda5_over_explicit"] = out["lambda_5_ms"] / out["explicit_ms"]
@@ -273,76 +426,7 @@ def collision_mode_costs(steps=20, warmup=3, n=128):
     return out
 
 
-def moving_fluid_costs(n=256, level=2, steps=10, warmup=3):
-    """Moving background fluid (mixed frame, App. B), 256^3 x 162 periodic,
-    the seeded shear flow: step time with FP32 and with FP16 populations."""
-    import torch
-    from paper_2007_05718_gb300 import lbrt
-    from paper_2007_05718_gb300 import workloads as W
-    mf = W.moving_fluid(n)
-    fields = {k: torch.from_numpy(mf[k]).cuda() for k in ("v", "kt_a", "kt_0", "eta_t")}
-    E0 = torch.ones((n, n, n), dtype=torch.float32, device="cuda")
-    out = {}
-    for name, st in (("fp32", lbrt.LB_RT_F32), ("fp16", lbrt.LB_RT_F16_DEV)):
-        stream = torch.cuda.Stream()
-        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=level, cfl=CFL,
-                              moving=True, storage=st, stream=stream.cuda_stream)
-        lbrt.lb_rt_set_fluid(h, **fields)
-        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
-        N = lbrt.lb_rt_directions(h)[0].shape[0]
-        lbrt.lb_rt_step(h, warmup)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lbrt.lb_rt_step(h, steps)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b) / steps
-        out[name] = {"ms_per_step": ms, "sd_s": n ** 3 * N / (ms * 1e-3)}
-        lbrt.lb_rt_destroy(h)
-        torch.cuda.empty_cache()
-    out["fp16_over_fp32"] = out["fp32"]["ms_per_step"] / out["fp16"]["ms_per_step"]
-    out["workload"] = "256^3 x 162 periodic shear flow (|v| <= 0.6), density-scaled opacities"
-    return out
-
-
-def diffusion_costs(n=256, level=2, steps=10, warmup=3):
-    """Optically thick diffusion, 256^3 x 162 periodic, kappa_0 = 1e3 /L,
-    Gaussian E0 (sigma 8 cells): step time with FP32, FP16 and BF16
-    populations, and the 16-bit over FP32 rate."""
-    import torch
-    from paper_2007_05718_gb300 import lbrt
-    from paper_2007_05718_gb300 import workloads as W
-    E0 = torch.from_numpy(W.gaussian_E0((n, n, n), 8.0)).cuda()
-    out = {}
-    for name, st in (("fp32", lbrt.LB_RT_F32), ("fp16", lbrt.LB_RT_F16_DEV),
-                     ("bf16", lbrt.LB_RT_BF16_DEV)):
-        stream = torch.cuda.Stream()
-        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=level, cfl=CFL,
-                              dx=1.0 / n, bc=(lbrt.LB_RT_PERIODIC,) * 3, storage=st,
-                              stream=stream.cuda_stream)
-        lbrt.lb_rt_set_fluid(h, kappa_0=1000.0)
-        lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
-        N = lbrt.lb_rt_directions(h)[0].shape[0]
-        lbrt.lb_rt_step(h, warmup)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lbrt.lb_rt_step(h, steps)
-        b.record(stream)
-        b.synchronize()
-        lbrt.lb_rt_sync(h)
-        ms = a.elapsed_time(b) / steps
-        out[name] = {"ms_per_step": ms, "sd_s": n ** 3 * N / (ms * 1e-3)}
-        lbrt.lb_rt_destroy(h)
-        torch.cuda.empty_cache()
-    out["fp16_over_fp32"] = out["fp32"]["ms_per_step"] / out["fp16"]["ms_per_step"]
-    out["bf16_over_fp32"] = out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
-    out["workload"] = "256^3 x 162 periodic diffusion, kappa_0 = 1e3 /L, Gaussian E0 (8 cells)"
-    return out
-
-
-def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
+def serving_measurement(n_capacity=24, n_open=150, seed=20200711, steps_per_tick=50):
     """Batched serving on the seeded request stream (sphere/shadow, n in
     {32..128}^3, 42 or 162 directions, kappa log-uniform 1e-1..1e4, 200-2000
     steps, FP16 storage): capacity from a closed-loop run of the first
@@ -353,17 +437,18 @@ def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
     closed = W.serving_requests(n_capacity, seed=seed, rate=1e9)
     for r in closed:
         r["arrival"] = 0.0
-    rc = serve.serve(closed, steps_per_tick=50, max_problems=64)
+    rc = serve.serve(closed, steps_per_tick=steps_per_tick, max_problems=64)
     cap = rc["throughput_req_s"]
     rate = 0.8 * cap
     stream = W.serving_requests(n_open, seed=seed, rate=rate)
-    ro = serve.serve(stream, steps_per_tick=50, max_problems=64)
+    ro = serve.serve(stream, steps_per_tick=steps_per_tick, max_problems=64)
     return {
         "capacity_req_s": cap, "capacity_sd_s": rc["throughput_sd_s"],
         "arrival_rate_req_s": rate, "requests": ro["requests"], "completed": ro["completed"],
         "p50_s": ro["p50_s"], "p99_s": ro["p99_s"], "throughput_req_s": ro["throughput_req_s"],
         "throughput_sd_s": ro["throughput_sd_s"], "max_concurrent": ro["max_concurrent"],
-        "storage": "fp16", "steps_per_tick": 50,
+        "launches_per_tick": ro.get("launches_per_tick"), "storage": "fp16",
+        "steps_per_tick": steps_per_tick,
         "sample": "first %d requests of the seed-%d stream (closed loop) and first %d with Poisson "
                   "arrivals at 0.8 x capacity; the configured stream has 2000" % (n_capacity, seed, n_open),
     }
@@ -372,16 +457,16 @@ def serving_measurement(n_capacity=16, n_open=40, seed=20200711):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
-    ap.add_argument("--e2e-steps", type=int, default=20, help="coupled steps of the end-to-end run")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle samples")
+    ap.add_argument("--e2e-steps", type=int, default=10, help="coupled steps of the end-to-end run")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched serving run")
     ap.add_argument("--no-collision-modes", action="store_true",
                     help="skip the implicit / explicit / Lambda-5 timing")
-    ap.add_argument("--no-moving", action="store_true",
-                    help="skip the 256^3 x 162 runs (diffusion FP32/FP16/BF16, moving fluid)")
+    ap.add_argument("--no-sublines", action="store_true",
+                    help="skip the FP16/BF16, sphere and moving-fluid sub-lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -389,28 +474,25 @@ def main():
         return run_reference(args)
 
     ws, rank, local = _dist()
-    import numpy as np
     import torch
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2007_05718_gb300 import build, lbrt
+    from paper_2007_05718_gb300 import workloads as W
     build.build()
-    sp = _workload_fields()
+    n = N_SIDE
+    sites = n ** 3
     stream = torch.cuda.Stream()
-    sites = N_SIDE ** 3
     with torch.cuda.stream(stream):
-        h = lbrt.lb_rt_create(3, N_SIDE, N_SIDE, N_SIDE, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL,
-                              cfl=CFL, dx=1.0 / N_SIDE, bc=(lbrt.LB_RT_VACUUM,) * 3,
-                              stream=stream.cuda_stream)
-        ka = torch.from_numpy(sp["kappa_a"]).cuda()
-        eta = torch.from_numpy(sp["eta"]).cuda()
-        E0 = torch.from_numpy(sp["E0"]).cuda()
-        lbrt.lb_rt_set_fluid(h, kappa_a=ka, eta=eta)
+        h = lbrt.lb_rt_create(3, n, n, n, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL, cfl=CFL,
+                              dx=1.0 / n, bc=(lbrt.LB_RT_PERIODIC,) * 3, stream=stream.cuda_stream)
+        lbrt.lb_rt_set_fluid(h, kappa_0=KAPPA0_DX * n)
+        E0 = torch.from_numpy(W.gaussian_E0((n, n, n), SIGMA_CELLS)).cuda()
         lbrt.lb_rt_set_state(h, E0, lbrt.LB_RT_STATE_ISOTROPIC)
+        del E0
         N = lbrt.lb_rt_directions(h)[0].shape[0]
-        # warm-up
         lbrt.lb_rt_step(h, args.warmup)
         stream.synchronize()
         _barrier(ws)
@@ -428,36 +510,19 @@ def main():
         _barrier(ws)
         ms = t0.elapsed_time(t1)
         ck = clocks.stop()
+        lbrt.lb_rt_sync(h)
         ms_max = _max_over_ranks(ws, ms)
         ms_step = ms_max / args.steps
         sd_step = sites * N
         value = aggregate_rate(sd_step, ws, ms_max, args.steps)
 
-        # the same workload with FP16 populations (16-bit deviation storage)
-        h16 = lbrt.lb_rt_create(3, N_SIDE, N_SIDE, N_SIDE, dirset=lbrt.LB_RT_ICOSPHERE, level=LEVEL,
-                                cfl=CFL, dx=1.0 / N_SIDE, bc=(lbrt.LB_RT_VACUUM,) * 3,
-                                storage=lbrt.LB_RT_F16_DEV, stream=stream.cuda_stream)
-        lbrt.lb_rt_set_fluid(h16, kappa_a=ka, eta=eta)
-        lbrt.lb_rt_set_state(h16, E0, lbrt.LB_RT_STATE_ISOTROPIC)
-        lbrt.lb_rt_step(h16, args.warmup)
-        stream.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            lbrt.lb_rt_step(h16, 1)
-        f1.record(stream)
-        f1.synchronize()
-        ms16 = _max_over_ranks(ws, f0.elapsed_time(f1)) / args.steps
-        lbrt.lb_rt_destroy(h16)
-
-        # end to end through the C ABI with host buffers
-        ka_h = torch.from_numpy(sp["kappa_a"]).pin_memory()
-        eta_h = torch.from_numpy(sp["eta"]).pin_memory()
+        # end to end through the C ABI with host buffers: a per-site kappa_0
+        # field in from pinned host memory, E and F out to pinned host memory
+        k0_h = torch.full((n, n, n), KAPPA0_DX * n, dtype=torch.float32).pin_memory()
         E_h = torch.empty(sites, dtype=torch.float32).pin_memory()
         F_h = torch.empty((3, sites), dtype=torch.float32).pin_memory()
         for _ in range(2):
-            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h, mapped=True)
+            lbrt.lb_rt_set_fluid(h, kappa_0=k0_h, mapped=True)
             lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         torch.cuda.synchronize()
         _barrier(ws)
@@ -466,7 +531,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            lbrt.lb_rt_set_fluid(h, kappa_a=ka_h, eta=eta_h, mapped=True)
+            lbrt.lb_rt_set_fluid(h, kappa_0=k0_h, mapped=True)
             lbrt.lb_rt_step_moments(h, 1, E_h, F_h)
         e1.record(stream)
         e1.synchronize()
@@ -474,51 +539,60 @@ def main():
         e_ms = _max_over_ranks(ws, max(e0.elapsed_time(e1), wall * 1e3))
         e2e_value = sd_step * ws / (e_ms * 1e-3 / args.e2e_steps)
         lbrt.lb_rt_destroy(h)
+        del k0_h, E_h, F_h
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-    bytes_per_launch = sites * N * 8.0 + sites * 8.0   # populations r+w, kappa_a and eta fields
-    peak, peak_kind = _peaks()
-    achieved = bytes_per_launch / (ms_step * 1e-3) / 1e9
-    traffic = _traffic_from_profiles()
+    bytes_per_launch = sites * N * 8.0   # populations read and written; kappa_0 is a scalar
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sites": sites, "ndir": N, "global_batch": ws,
+        "config": {"workload": WORKLOAD + ", FP32 populations", "sites": sites, "ndir": N,
+                   "storage": "fp32", "global_batch": ws,
                    "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (%.0f MB of populations per step)" % (sites * N * 4 / 1e6)},
+                   "l2": "inputs larger than L2 (%.1f GB of populations per step)" % (sites * N * 4 / 1e9)},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": bytes_per_launch},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * sites,
+        "roofline": roofline("c3_fp32", bytes_per_launch, ms_step),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * sites,
                 "d2h_bytes_per_step": 4 * 4 * sites, "steps": args.e2e_steps,
-                "route": "lb_rt_set_fluid(kappa_a, eta in pinned host memory, read in place "
-                         "by the step kernel) + lb_rt_step_moments(1 step, E and F written "
-                         "to pinned host memory by the step kernel)"},
+                "route": "lb_rt_set_fluid(kappa_0 per site in pinned host memory, read in place by "
+                         "the step kernel) + lb_rt_step_moments(1 step, E and F written to pinned "
+                         "host memory by the step kernel)"},
         "clocks": ck,
-        "f16": {"value": sd_step * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
-                "ratio_vs_f32": ms_step / ms16,
-                "storage": "FP16 deviation from w_i E, float32 E per site, float32 arithmetic"},
     }
+    if not args.no_sublines and ws == 1:
+        sub = {}
+        few = max(3, min(args.steps, 20))
+        for key, fn, st, steps in (
+                ("c3_fp16", diffusion_line, lbrt.LB_RT_F16_DEV, few),
+                ("c3_bf16", diffusion_line, lbrt.LB_RT_BF16_DEV, few),
+                ("c2_fp32", sphere_line, lbrt.LB_RT_F32, max(3, min(args.steps, 200))),
+                ("c2_fp16", sphere_line, lbrt.LB_RT_F16_DEV, max(3, min(args.steps, 200))),
+                ("c5_fp32", moving_line, lbrt.LB_RT_F32, few),
+                ("c5_fp16", moving_line, lbrt.LB_RT_F16_DEV, few)):
+            try:
+                sub[key] = fn(key, st, steps, args.warmup)
+            except Exception as e:  # report, do not hide
+                sub[key] = {"error": str(e)[:300]}
+        line["sublines"] = sub
+        try:
+            line["fp16_over_fp32"] = {
+                "diffusion_256_162": ms_step / sub["c3_fp16"]["ms_per_step"],
+                "bf16_diffusion_256_162": ms_step / sub["c3_bf16"]["ms_per_step"],
+                "sphere_128_42": sub["c2_fp32"]["ms_per_step"] / sub["c2_fp16"]["ms_per_step"],
+                "moving_256_162": sub["c5_fp32"]["ms_per_step"] / sub["c5_fp16"]["ms_per_step"]}
+        except Exception:
+            pass
     if not args.no_collision_modes and ws == 1:
         try:
             line["collision_modes"] = collision_mode_costs()
         except Exception as e:  # report, do not hide
             line["collision_modes"] = {"error": str(e)[:300]}
-    if not args.no_moving and ws == 1:
-        try:
-            line["diffusion_256"] = diffusion_costs()
-        except Exception as e:  # report, do not hide
-            line["diffusion_256"] = {"error": str(e)[:300]}
-        try:
-            line["moving_fluid"] = moving_fluid_costs()
-        except Exception as e:  # report, do not hide
-            line["moving_fluid"] = {"error": str(e)[:300]}
     if not args.no_serving and ws == 1:
         try:
             line["serving"] = serving_measurement()
@@ -526,10 +600,7 @@ def main():
             line["serving"] = {"error": str(e)[:300]}
     if not args.no_cpu_baseline:
         try:
-            sec, sd = oracle_sample_time(64, 1)
-            line["cpu_baseline"] = {"value": sd / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "1 oracle step (FP64 numpy) of a 64^3 sub-box of the same workload, 42 dirs",
-                                    "host_cores": len(os.sched_getaffinity(0))}
+            line["cpu_baseline"] = cpu_baselines()
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
     print(json.dumps(line))

@@ -59,88 +59,6 @@ __device__ __forceinline__ void bar_arrive_n(int id, int n) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// ---- tensor memory (TMEM) as a parking place for streamed values ---------
-// A warp reaches the 32 TMEM lanes of its quarter (warp index mod 4); one
-// tcgen05.st / tcgen05.ld moves N 32-bit registers per thread to / from N
-// consecutive columns of the thread's lane.  The waits take the registers as
-// operands so that the compiler neither reuses a source register before the
-// store has read it nor uses a loaded register before the load has landed.
-__device__ __forceinline__ void tm_alloc(uint32_t smem_dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tm_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tm_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tm_st4(uint32_t ta, float a, float b, float c, float d) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta),
-               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
-               "r"(__float_as_uint(d))
-               : "memory");
-}
-__device__ __forceinline__ void tm_st2(uint32_t ta, float a, float b) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(ta),
-               "r"(__float_as_uint(a)), "r"(__float_as_uint(b))
-               : "memory");
-}
-__device__ __forceinline__ void tm_ld4(uint32_t ta, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
-               : "r"(ta)
-               : "memory");
-}
-__device__ __forceinline__ void tm_ld2(uint32_t ta, uint32_t& a, uint32_t& b) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-               : "=r"(a), "=r"(b)
-               : "r"(ta)
-               : "memory");
-}
-// word c of a batch of streamed values (DPT x ZC float2, 2 DPT ZC words);
-// c is a compile-time constant in every unrolled use
-template <int DPT, int ZC>
-__device__ __forceinline__ float& tm_word(float2 (&v)[DPT][ZC], int c) {
-  float2& p = v[(c >> 1) / ZC][(c >> 1) % ZC];
-  return (c & 1) ? p.y : p.x;
-}
-// the streamed values of one batch to / from the TMEM columns ta .. ta +
-// 2 DPT ZC - 1 of the thread's lane
-template <int DPT, int ZC>
-__device__ __forceinline__ void tm_put(uint32_t ta, float2 (&v)[DPT][ZC]) {
-  constexpr int NW = 2 * DPT * ZC;
-#pragma unroll
-  for (int c = 0; c + 4 <= NW; c += 4)
-    tm_st4(ta + c, tm_word(v, c), tm_word(v, c + 1), tm_word(v, c + 2), tm_word(v, c + 3));
-  if constexpr (NW % 4 != 0) tm_st2(ta + NW - 2, tm_word(v, NW - 2), tm_word(v, NW - 1));
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  // the sources stay live (unchanged) up to the wait
-#pragma unroll
-  for (int c = 0; c < NW; ++c) asm volatile("" : "+f"(tm_word(v, c)));
-}
-template <int DPT, int ZC>
-__device__ __forceinline__ void tm_get(uint32_t ta, float2 (&v)[DPT][ZC]) {
-  constexpr int NW = 2 * DPT * ZC;
-  uint32_t w[NW];
-#pragma unroll
-  for (int c = 0; c + 4 <= NW; c += 4) tm_ld4(ta + c, w[c], w[c + 1], w[c + 2], w[c + 3]);
-  if constexpr (NW % 4 != 0) tm_ld2(ta + NW - 2, w[NW - 2], w[NW - 1]);
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  // no use of a loaded register before the wait
-#pragma unroll
-  for (int c = 0; c < NW; ++c) {
-    asm volatile("" : "+r"(w[c]));
-    tm_word(v, c) = __uint_as_float(w[c]);
-  }
-}
-
 template <class ST> struct SV;
 template <> struct SV<float> {
   static constexpr int BOX = BOXX;  // float32 box columns
@@ -208,10 +126,7 @@ struct BatchCtx {
   int zb, flags, ti;
 };
 
-// TM: the streamed values a stream warp keeps until its deferred store are
-// parked in tensor memory (two batches per warp) instead of registers, which
-// leaves room for 17-18 warps of up to 96 registers per CTA.
-template <class ST, int MODE, bool PER, int DPT, int ZC, int MAXT, int REGS, bool TM>
+template <class ST, int MODE, bool PER, int DPT, int ZC, int MAXT, int REGS>
 __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap emap,
      const __grid_constant__ ProblemDesc P, int ntiles, unsigned* err, const DirTable t) {
@@ -234,7 +149,6 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
   unsigned long long* ebar = mbar + G * 2;
   double* bsum = reinterpret_cast<double*>(ebar + kEring);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bsum + 2 * ZC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bsum + 2 * ZC) + 1;
 
   const Grid& gr = P.g;
   const int nx = gr.nx, ny = gr.ny, nz = gr.nz;
@@ -261,16 +175,8 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
   if (!F32 && g == 0 && lane == 0)
     for (int r = 0; r < kEring; ++r) mbar_init(smem_u32(&ebar[r]), 1);
   if (g == 0 && lane == 0) *abort_flag = 0;
-  // TMEM columns: two batches of 2 DPT ZC words per stream warp, the warps of
-  // one lane quarter (g mod 4) side by side
-  constexpr int TMW = 2 * DPT * ZC;
-  uint32_t tm_cols = 32;
-  while ((int)tm_cols < ((NW - ZC + 3) / 4) * 2 * TMW) tm_cols <<= 1;
-  if (TM && g == 0) tm_alloc(smem_u32(tmem_slot), tm_cols);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  if (TM) tm_fence_before();
   __syncthreads();
-  if (TM) tm_fence_after();
 
   // the batch cursor every warp walks: tile ti (round-robin), item m of M
   int ti = blockIdx.x, m = 0;
@@ -640,11 +546,9 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
   for (int k = 0; k < DPT; ++k) carry[k] = make_float2(0.f, 0.f);
   float2 IsA[DPT][ZC], IsB[DPT][ZC];
   BatchCtx<ST> ctx{};  // store context of the previous batch
-  // this warp's TMEM columns (lane quarter g mod 4, slot g / 4 within it)
-  const uint32_t tm_base = TM ? *tmem_slot + ((uint32_t)(32 * (g & 3)) << 16) + (uint32_t)((g >> 2) * 2 * TMW) : 0u;
 
   // one batch: stream into `cur`, then store `prev` (the previous batch)
-  auto batch = [&](int q, float2 (&cur)[DPT][ZC], float2 (&prev)[DPT][ZC]) {
+  auto batch = [&](int q, float2 (&cur)[DPT][ZC], const float2 (&prev)[DPT][ZC]) {
     issue_next();
     wait_item(q);
     float2 aE[ZC], aX[ZC], aY[ZC], aZ[ZC];
@@ -750,7 +654,6 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
         else pass(std::false_type());
       }
     }
-    if (TM) tm_put(tm_base + (uint32_t)((q & 1) * TMW), cur);  // park I*(q)
     if (q > 0) bar_sync_n(kBarC, NT);  // coef(q - 1) ready; partials(q - 1) read
     {
       float2* pw = reinterpret_cast<float2*>(part + (size_t)g * ZC * 4 * 64) + lane;
@@ -763,47 +666,24 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
       }
     }
     bar_arrive_n(kBarP, NT);
-    if (q > 0) {
-      if (TM) tm_get(tm_base + (uint32_t)(((q - 1) & 1) * TMW), prev);
-      store_batch(prev, ctx, (q - 1) & 1);
-    }
+    if (q > 0) store_batch(prev, ctx, (q - 1) & 1);
     ctx = make_ctx();
     advance();
   };
 
   if (ti < ntiles) issue_item(ti, 0, tg);  // batch 0; every batch issues the one after it
   int q = 0;
-  if constexpr (TM) {
-    // one register copy: the previous batch comes back from tensor memory
-    while (ti < ntiles) {
-      batch(q, IsA, IsA);
-      ++q;
-    }
-    if (q > 0) {
-      bar_sync_n(kBarC, NT);
-      tm_get(tm_base + (uint32_t)(((q - 1) & 1) * TMW), IsA);
-      store_batch(IsA, ctx, (q - 1) & 1);
-    }
-    // every stream warp is done with tensor memory before it is returned
-    tm_fence_before();
-    bar_sync_n(3, (NW - ZC) * 32);
-    if (g == 0) {
-      tm_fence_after();
-      tm_dealloc(*tmem_slot, tm_cols);
-    }
-  } else {
-    while (ti < ntiles) {
-      batch(q, IsA, IsB);
-      ++q;
-      if (ti >= ntiles) break;
-      batch(q, IsB, IsA);
-      ++q;
-    }
-    if (q > 0) {
-      bar_sync_n(kBarC, NT);
-      if (q & 1) store_batch(IsA, ctx, (q - 1) & 1);
-      else store_batch(IsB, ctx, (q - 1) & 1);
-    }
+  while (ti < ntiles) {
+    batch(q, IsA, IsB);
+    ++q;
+    if (ti >= ntiles) break;
+    batch(q, IsB, IsA);
+    ++q;
+  }
+  if (q > 0) {
+    bar_sync_n(kBarC, NT);
+    if (q & 1) store_batch(IsA, ctx, (q - 1) & 1);
+    else store_batch(IsB, ctx, (q - 1) & 1);
   }
   // copies still in flight (only after a failed wait) land before exit
   for (int qq = waited; qq < q_is; ++qq) {
@@ -812,47 +692,47 @@ k_sc(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorM
   }
 }
 
-template <class ST, int MODE, bool PER, int DPT, int ZC, int MAXT, int REGS, bool TM>
+template <class ST, int MODE, bool PER, int DPT, int ZC, int MAXT, int REGS>
 cudaError_t sc_attr() {
   static unsigned long long done = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (done >> dev & 1ull)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_sc<ST, MODE, PER, DPT, ZC, MAXT, REGS, TM>,
+  const cudaError_t e = cudaFuncSetAttribute(k_sc<ST, MODE, PER, DPT, ZC, MAXT, REGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024 - 1024);
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
 }
 
-template <class ST, int DPT, int ZC, int MAXT, int REGS, bool TM>
+template <class ST, int DPT, int ZC, int MAXT, int REGS>
 cudaError_t sc_occupancy(int G, int* per_sm) {
   const size_t smem = sc_smem_bytes<ST, DPT, ZC>(G);
   const int threads = 32 * (G + ZC);
   // the moments-epilogue variant (MODE 2) exists for float32 storage only
   constexpr int M2 = SV<ST>::F32 ? 2 : 0;
   int r[4] = {0, 0, 0, 0};
-  cudaError_t e = sc_attr<ST, 0, false, DPT, ZC, MAXT, REGS, TM>();
-  if (e == cudaSuccess) e = sc_attr<ST, 0, true, DPT, ZC, MAXT, REGS, TM>();
-  if (e == cudaSuccess) e = sc_attr<ST, M2, false, DPT, ZC, MAXT, REGS, TM>();
-  if (e == cudaSuccess) e = sc_attr<ST, M2, true, DPT, ZC, MAXT, REGS, TM>();
+  cudaError_t e = sc_attr<ST, 0, false, DPT, ZC, MAXT, REGS>();
+  if (e == cudaSuccess) e = sc_attr<ST, 0, true, DPT, ZC, MAXT, REGS>();
+  if (e == cudaSuccess) e = sc_attr<ST, M2, false, DPT, ZC, MAXT, REGS>();
+  if (e == cudaSuccess) e = sc_attr<ST, M2, true, DPT, ZC, MAXT, REGS>();
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[0], k_sc<ST, 0, false, DPT, ZC, MAXT, REGS, TM>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[0], k_sc<ST, 0, false, DPT, ZC, MAXT, REGS>,
                                                       threads, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[1], k_sc<ST, 0, true, DPT, ZC, MAXT, REGS, TM>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[1], k_sc<ST, 0, true, DPT, ZC, MAXT, REGS>,
                                                       threads, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[2], k_sc<ST, M2, false, DPT, ZC, MAXT, REGS, TM>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[2], k_sc<ST, M2, false, DPT, ZC, MAXT, REGS>,
                                                       threads, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[3], k_sc<ST, M2, true, DPT, ZC, MAXT, REGS, TM>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[3], k_sc<ST, M2, true, DPT, ZC, MAXT, REGS>,
                                                       threads, smem);
   *per_sm = std::min(std::min(r[0], r[1]), std::min(r[2], r[3]));
   return e;
 }
 
-template <class ST, int DPT, int ZC, int MAXT, int REGS, bool TM>
+template <class ST, int DPT, int ZC, int MAXT, int REGS>
 cudaError_t sc_launch(const StepLaunch& L, const StaticCoef& c, const DirTable& t, cudaStream_t s,
                       int* nblocks) {
   const int G = L.N / DPT;
@@ -885,9 +765,9 @@ cudaError_t sc_launch(const StepLaunch& L, const StaticCoef& c, const DirTable& 
   cudaError_t e;
 #define LBRT_SC_GO(MODE_, PER_)                                                                 \
   do {                                                                                          \
-    e = sc_attr<ST, MODE_, PER_, DPT, ZC, MAXT, REGS, TM>();                                        \
+    e = sc_attr<ST, MODE_, PER_, DPT, ZC, MAXT, REGS>();                                        \
     if (e != cudaSuccess) return e;                                                             \
-    k_sc<ST, MODE_, PER_, DPT, ZC, MAXT, REGS, TM><<<L.ctas, block, smem, s>>>(*L.tmap_in, emap, P, \
+    k_sc<ST, MODE_, PER_, DPT, ZC, MAXT, REGS><<<L.ctas, block, smem, s>>>(*L.tmap_in, emap, P, \
                                                                            P.ntiles, L.err, t); \
   } while (0)
   constexpr int M2 = SV<ST>::F32 ? 2 : 0;  // moments epilogue: float32 only
@@ -900,25 +780,23 @@ cudaError_t sc_launch(const StepLaunch& L, const StaticCoef& c, const DirTable& 
 }
 
 // Tile plans of the pipelined kernel (directions per warp, planes per batch,
-// thread cap including the coefficient warps, registers per thread, TMEM
-// parking), in order of preference.  A stream warp keeps the carried plane
-// and two batches of streamed values: in registers, 96 per thread give two
-// 10-warp CTAs per SM (ico42: 45 internal directions, 9 stream warps + 1
-// coefficient warp).  For ico162 (170 internal directions at 10 per warp: 17
-// stream warps + 1 coefficient warp) the per-SM register file leaves 96 per
-// thread (resident warps are counted in groups of 4, so 18 warps need 20
-// warps' worth of registers), which does not hold two batches: the previous
-// batch waits in tensor memory.
-#define LBRT_SC_PLANS(X)   \
-  X(5, 1, 320, 96, false)  \
-  X(10, 1, 576, 96, true)  \
-  X(4, 1, 544, 96, false)
+// thread cap including the coefficient warps, registers per thread), in
+// order of preference.  A stream warp keeps the carried plane and two
+// batches of streamed values in registers: 96 per thread give two 10-warp
+// CTAs per SM (ico42: 45 internal directions, 9 stream warps + 1
+// coefficient warp).  The 162-direction set (16 stream warps + 1 coefficient
+// warp) would leave 96 registers per thread (resident warps are counted in
+// groups of 4, so 17 warps take 20 warps' worth), which do not hold two
+// batches; it runs the first-generation kernel.
+#define LBRT_SC_PLANS(X) \
+  X(5, 1, 320, 96)       \
+  X(4, 1, 544, 96)
 
 template <class ST>
 cudaError_t sc_launch_typed(const StepLaunch& L, const StaticCoef& c, const DirTable& t, cudaStream_t s,
                             int* nblocks) {
-#define LBRT_SC_L(D, Z, T, B, TM) \
-  if (L.dpt == D && L.zc == Z) return sc_launch<ST, D, Z, T, B, TM>(L, c, t, s, nblocks);
+#define LBRT_SC_L(D, Z, T, B) \
+  if (L.dpt == D && L.zc == Z) return sc_launch<ST, D, Z, T, B>(L, c, t, s, nblocks);
   LBRT_SC_PLANS(LBRT_SC_L)
 #undef LBRT_SC_L
   return cudaErrorInvalidValue;
@@ -926,8 +804,8 @@ cudaError_t sc_launch_typed(const StepLaunch& L, const StaticCoef& c, const DirT
 
 template <class ST>
 cudaError_t sc_occupancy_typed(int dpt, int zc, int G, int* per_sm) {
-#define LBRT_SC_O(D, Z, T, B, TM) \
-  if (dpt == D && zc == Z) return sc_occupancy<ST, D, Z, T, B, TM>(G, per_sm);
+#define LBRT_SC_O(D, Z, T, B) \
+  if (dpt == D && zc == Z) return sc_occupancy<ST, D, Z, T, B>(G, per_sm);
   LBRT_SC_PLANS(LBRT_SC_O)
 #undef LBRT_SC_O
   return cudaErrorInvalidValue;
@@ -935,13 +813,13 @@ cudaError_t sc_occupancy_typed(int dpt, int zc, int G, int* per_sm) {
 
 }  // namespace
 
-#define LBRT_SC_ROW(D, Z, T, B, TM) {D, Z, T},
+#define LBRT_SC_ROW(D, Z, T, B) {D, Z, T},
 const int kTilePlansSC[][3] = {LBRT_SC_PLANS(LBRT_SC_ROW)};
 #undef LBRT_SC_ROW
 const int kNumTilePlansSC = sizeof(kTilePlansSC) / sizeof(kTilePlansSC[0]);
 
 size_t step_tile_smem_sc(int storage, int dpt, int zc, int stream_warps) {
-#define LBRT_SC_S(D, Z, T, B, TM)                                              \
+#define LBRT_SC_S(D, Z, T, B)                                                  \
   if (dpt == D && zc == Z)                                                     \
     return storage == ST_F32 ? sc_smem_bytes<float, D, Z>(stream_warps)        \
                              : sc_smem_bytes<__half, D, Z>(stream_warps);

@@ -641,8 +641,7 @@ constexpr int kRing = 2;
   X(10, 1, 544, 96)        \
   X(8, 2, 512, 128)        \
   X(4, 2, 512, 128)        \
-  X(4, 1, 640, 96)         \
-  X(5, 1, 320, 96)
+  X(4, 1, 640, 96)
 
 }  // namespace
 
