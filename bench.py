@@ -447,7 +447,7 @@ def serving_measurement(n_capacity=24, n_open=150, seed=20200711, steps_per_tick
         "arrival_rate_req_s": rate, "requests": ro["requests"], "completed": ro["completed"],
         "p50_s": ro["p50_s"], "p99_s": ro["p99_s"], "throughput_req_s": ro["throughput_req_s"],
         "throughput_sd_s": ro["throughput_sd_s"], "max_concurrent": ro["max_concurrent"],
-        "launches_per_tick": ro.get("launches_per_tick"), "storage": "fp16",
+        "ticks": ro["ticks"], "storage": "fp16",
         "steps_per_tick": steps_per_tick,
         "sample": "first %d requests of the seed-%d stream (closed loop) and first %d with Poisson "
                   "arrivals at 0.8 x capacity; the configured stream has 2000" % (n_capacity, seed, n_open),

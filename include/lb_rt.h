@@ -304,15 +304,18 @@ size_t lb_rt_batch_problem_bytes(const lb_rt_batch* b, const lb_rt_config* cfg);
  * from the batch; moving and budget must be 0), its fluid fields and
  * initial state as for lb_rt_set_fluid / lb_rt_set_state, and the number of
  * steps to run.  *slot receives its slot.  Errors: EINVAL, EBUSY (does not
- * fit now), ENOMEM, ECUDA. */
+ * fit now), ENOMEM, ECUDA.  The problem's initial state and fields are set
+ * on a stream of its own, so an admission overlaps the ticks in flight. */
 lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb_rt_fluid* fluid,
                                int fluid_ptr_kind, const float* state, int state_kind,
                                int state_ptr_kind, long long nsteps, int* slot);
 
 /* Enqueue one tick: every active problem advances by min(steps_per_tick,
  * remaining steps).  *n_active (may be NULL) receives the number of
- * problems that took part.  Asynchronous on the batch stream (the call
- * first waits for the previous tick, whose tables it reuses). */
+ * problems that took part (0: nothing was enqueued).  Asynchronous on the
+ * batch stream: two ticks may be in flight; the call waits only for the
+ * tick before the previous one, whose descriptor tables it reuses.  A
+ * problem's first tick waits (on the device) for its admission work. */
 lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active);
 
 /* Wait for the enqueued ticks and surface device errors.  LB_RT_ETIMEDOUT
@@ -320,18 +323,22 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active);
  * state untrusted and the batch's error word set: destroy the batch. */
 lb_rt_status lb_rt_batch_sync(lb_rt_batch* b);
 
-/* Slots whose problems have run all their steps and are not yet released
- * (call after lb_rt_batch_sync).  Writes at most max slots; *n the count. */
+/* Slots whose problems have run all their steps on the device (the tick
+ * with the last step has completed) and are not yet released; does not
+ * wait.  Writes at most max slots; *n the count. */
 lb_rt_status lb_rt_batch_poll(lb_rt_batch* b, int* slots, int max, int* n);
 
-/* Moments of a problem's current state, as lb_rt_moments (budget NULL). */
+/* Moments of a problem's current state, as lb_rt_moments (budget NULL);
+ * waits for the ticks enqueued so far. */
 lb_rt_status lb_rt_batch_moments(lb_rt_batch* b, int slot, float* E, float* F, float* P,
                                  int ptr_kind);
 
-/* Steps done by the problem in `slot`. */
+/* Steps enqueued for the problem in `slot` (done once poll reports it). */
 lb_rt_status lb_rt_batch_steps(const lb_rt_batch* b, int slot, long long* steps);
 
-/* Free a problem's device memory and its slot. */
+/* Free a problem's slot.  Its device memory goes back to the batch at the
+ * next lb_rt_batch_sync(), or at an admission that needs the room (its last
+ * tick may still be in flight when the slot is released). */
 lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot);
 
 /* The autotuner's current choice for the group of `slot`: z-chunk length

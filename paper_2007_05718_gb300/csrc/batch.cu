@@ -22,6 +22,9 @@ struct Member {
   size_t bytes = 0;
   int group = -1;
   bool used = false;
+  cudaEvent_t ready = nullptr;  // admission work (on the problem's own stream) done
+  bool joined = false;          // the batch stream has waited for `ready`
+  long long done_tick = -1;     // tick that enqueued the problem's last step
 };
 
 // Problems that share the internal direction table, tile plan and storage.
@@ -52,21 +55,32 @@ struct lb_rt_batch {
   int sms = 0;
   std::vector<Member> slots;
   std::vector<Group> groups;
-  // descriptor tables: host staging (pinned) and device copy
-  ProblemDesc* h_desc = nullptr;
-  ProblemDesc* d_desc = nullptr;
-  size_t desc_cap = 0;
+  // descriptor tables, one pair per tick parity (host staging, pinned, and
+  // device copy): tick t fills pair t & 1 once tick t - 2 has completed, so
+  // the host prepares a tick while the previous one runs
+  ProblemDesc* h_desc[2] = {nullptr, nullptr};
+  ProblemDesc* d_desc[2] = {nullptr, nullptr};
+  size_t desc_cap[2] = {0, 0};
+  static constexpr int kTickEvents = 4;
+  cudaEvent_t tick_ev[kTickEvents] = {nullptr, nullptr, nullptr, nullptr};  // end of tick t: [t % 4]
+  long long ticks = 0;   // ticks enqueued
+  // released problems whose device memory is returned at the next
+  // synchronisation (freeing right away would wait for the ticks in flight)
+  std::vector<lb_rt*> grave;
+  size_t grave_bytes = 0;
   // tensor maps of every slot: [slot][parity][pop, E]
   CUtensorMap* h_maps = nullptr;
   CUtensorMap* d_maps = nullptr;
   bool maps_dirty = true;
   unsigned* d_err = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // the launch plan the graph was captured for: per launch (group, first
-  // descriptor, problems, tiles) and per descriptor (slot, z chunks); a
-  // graph is replayed only for an identical plan
-  std::vector<long long> graph_sig;
+  // one graph per tick parity; the launch plan it was captured for: per
+  // launch (group, first descriptor, problems, tiles) and per descriptor
+  // (slot, z chunks); a graph is replayed only for an identical plan, and a
+  // changed plan updates the instantiated graph in place where the update
+  // applies
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<long long> graph_sig[2];
   std::string msg;
 };
 
@@ -87,6 +101,26 @@ lb_rt_status bcuda(lb_rt_batch* b, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                           \
     if (e_ != cudaSuccess) return bcuda(b, e_, #call); \
   } while (0)
+
+// true when tick t has completed on the device (ticks up to t_last - 2 have:
+// tick t_last waited for them before it was enqueued)
+bool tick_done(lb_rt_batch* b, long long t) {
+  if (t < 0 || t <= b->ticks - 3) return true;
+  const cudaError_t e = cudaEventQuery(b->tick_ev[t % lb_rt_batch::kTickEvents]);
+  if (e == cudaErrorNotReady) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// free the released problems (the caller has synchronised the batch stream)
+void flush_grave(lb_rt_batch* b) {
+  for (lb_rt* h : b->grave) lb_rt_destroy(h);
+  b->grave.clear();
+  b->used -= b->grave_bytes;
+  b->grave_bytes = 0;
+}
 
 bool same_table(const Group& g, const lb_rt* h) {
   return g.Ni == h->Ni && g.dpt == h->dpt && g.zc == h->zc &&
@@ -133,6 +167,8 @@ lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out
   if (e == cudaSuccess) std::memset(b->h_maps, 0, sizeof(CUtensorMap) * nmaps);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_maps, sizeof(CUtensorMap) * nmaps);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(unsigned));
+  for (int i = 0; i < lb_rt_batch::kTickEvents && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&b->tick_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -146,16 +182,23 @@ lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out
 void lb_rt_batch_destroy(lb_rt_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (auto& m : b->slots)
+  flush_grave(b);
+  for (auto& m : b->slots) {
     if (m.h) lb_rt_destroy(m.h);
+    if (m.ready) cudaEventDestroy(m.ready);
+  }
   for (auto& g : b->groups) {
     if (g.ev0) cudaEventDestroy(g.ev0);
     if (g.ev1) cudaEventDestroy(g.ev1);
   }
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFreeHost(b->h_desc);
-  cudaFree(b->d_desc);
+  for (int i = 0; i < 2; ++i) {
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+    cudaFreeHost(b->h_desc[i]);
+    cudaFree(b->d_desc[i]);
+  }
+  for (cudaEvent_t ev : b->tick_ev)
+    if (ev) cudaEventDestroy(ev);
   cudaFreeHost(b->h_maps);
   cudaFree(b->d_maps);
   cudaFree(b->d_err);
@@ -181,7 +224,7 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
     return bfail(b, LB_RT_EINVAL, "batched problems are static and keep no energy budget");
   lb_rt_config c = *cfg;
   c.storage = b->cfg.storage;
-  c.stream = b->stream;
+  c.stream = nullptr;  // the problem's own stream: admission overlaps the ticks in flight
   c.budget = 0;
   std::string err;
   const size_t bytes = handle_device_bytes(c, err);
@@ -193,6 +236,11 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
       break;
     }
   if (s < 0) return bfail(b, LB_RT_EBUSY, "no free slot");
+  if (b->used + bytes > b->budget && !b->grave.empty() && b->used - b->grave_bytes + bytes <= b->budget) {
+    // the memory of released problems makes room: return it now
+    BCK(b, cudaStreamSynchronize(b->stream));
+    flush_grave(b);
+  }
   if (b->used + bytes > b->budget)
     return bfail(b, LB_RT_EBUSY, "does not fit the memory budget now");
   lb_rt* h = nullptr;
@@ -231,12 +279,23 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
     b->groups.push_back(g);
     gi = (int)b->groups.size() - 1;
   }
+  cudaEvent_t ready = nullptr;
+  cudaError_t er = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (er == cudaSuccess) er = cudaEventRecord(ready, h->stream);
+  if (er != cudaSuccess) {
+    if (ready) cudaEventDestroy(ready);
+    lb_rt_destroy(h);
+    return bcuda(b, er, "admission event");
+  }
   Member& m = b->slots[s];
   m.h = h;
   m.nsteps = nsteps;
   m.bytes = bytes;
   m.group = gi;
   m.used = true;
+  m.ready = ready;
+  m.joined = false;
+  m.done_tick = -1;
   b->used += bytes;
   // tensor maps of both parities, copied to the device array at the next tick
   for (int par = 0; par < 2; ++par) {
@@ -252,8 +311,11 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
   if (!b) return LB_RT_EINVAL;
   const int K = b->cfg.steps_per_tick;
   const int G = (int)b->groups.size();
-  // the previous tick must have read the staging tables
-  BCK(b, cudaStreamSynchronize(b->stream));
+  const long long t = b->ticks;
+  const int buf = (int)(t & 1);
+  // tick t - 2 read the staging tables of this parity: wait for it (and
+  // for nothing later)
+  if (t >= 2) BCK(b, cudaEventSynchronize(b->tick_ev[(t - 2) % lb_rt_batch::kTickEvents]));
   // plan[k][g]: slots of group g that take step k of this tick
   std::vector<std::vector<std::vector<int>>> plan(K, std::vector<std::vector<int>>(G));
   int active = 0;
@@ -292,18 +354,24 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
   size_t ndesc = 0;
   for (int k = 0; k < K; ++k)
     for (int g = 0; g < G; ++g) ndesc += plan[k][g].size();
-  if (ndesc > b->desc_cap) {
-    cudaFreeHost(b->h_desc);
-    cudaFree(b->d_desc);
-    b->h_desc = nullptr;
-    b->d_desc = nullptr;
-    b->desc_cap = 0;
-    b->graph_sig.clear();  // a captured graph refers to the old tables
+  if (ndesc > b->desc_cap[buf]) {
+    cudaFreeHost(b->h_desc[buf]);
+    cudaFree(b->d_desc[buf]);
+    b->h_desc[buf] = nullptr;
+    b->d_desc[buf] = nullptr;
+    b->desc_cap[buf] = 0;
+    b->graph_sig[buf].clear();  // a captured graph refers to the old tables
+    if (b->exec[buf]) cudaGraphExecDestroy(b->exec[buf]);
+    if (b->graph[buf]) cudaGraphDestroy(b->graph[buf]);
+    b->exec[buf] = nullptr;
+    b->graph[buf] = nullptr;
     const size_t cap = std::max<size_t>(ndesc, 2 * b->slots.size());
-    BCK(b, cudaMallocHost((void**)&b->h_desc, sizeof(ProblemDesc) * cap));
-    BCK(b, cudaMalloc((void**)&b->d_desc, sizeof(ProblemDesc) * cap));
-    b->desc_cap = cap;
+    BCK(b, cudaMallocHost((void**)&b->h_desc[buf], sizeof(ProblemDesc) * cap));
+    BCK(b, cudaMalloc((void**)&b->d_desc[buf], sizeof(ProblemDesc) * cap));
+    b->desc_cap[buf] = cap;
   }
+  ProblemDesc* h_desc = b->h_desc[buf];
+  ProblemDesc* d_desc = b->d_desc[buf];
   std::vector<Launch> launches;
   std::vector<long long> sig;
   sig.push_back((long long)ndesc);
@@ -317,7 +385,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       for (int s : ms) {
         const lb_rt* h = b->slots[s].h;
         const int cur = (int)((h->cur + k) & 1);
-        ProblemDesc& d = b->h_desc[at++];
+        ProblemDesc& d = h_desc[at++];
         d = ProblemDesc{};
         d.g = h->grid;
         d.out = h->pop[cur ^ 1];
@@ -345,6 +413,14 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       sig.push_back(L.periodic);
     }
   }
+  // problems stepped for the first time: their admission (initial state,
+  // fields) ran on their own streams
+  for (int s = 0; s < (int)b->slots.size(); ++s) {
+    Member& m = b->slots[s];
+    if (!m.used || m.joined || m.nsteps - m.h->steps <= 0) continue;
+    BCK(b, cudaStreamWaitEvent(b->stream, m.ready, 0));
+    m.joined = true;
+  }
   // the tick's device work: table uploads, then one batched launch per
   // group and step
   auto enqueue = [&](bool timed) -> cudaError_t {
@@ -353,8 +429,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       e = cudaMemcpyAsync(b->d_maps, b->h_maps, sizeof(CUtensorMap) * 4 * b->slots.size(),
                           cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(ProblemDesc) * ndesc,
-                          cudaMemcpyHostToDevice, b->stream);
+      e = cudaMemcpyAsync(d_desc, h_desc, sizeof(ProblemDesc) * ndesc, cudaMemcpyHostToDevice,
+                          b->stream);
     for (int g = 0; g < G && e == cudaSuccess; ++g) {
       Group& gr = b->groups[g];
       const bool time_it = timed && !gr.tuned && group_sd[g] > 0;
@@ -362,7 +438,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       for (const Launch& L : launches) {
         if (L.group != g || e != cudaSuccess) continue;
         BatchLaunch B{};
-        B.table = b->d_desc + L.first;
+        B.table = d_desc + L.first;
         B.nprob = L.nprob;
         B.ntiles = L.ntiles;
         B.N = gr.Ni;
@@ -382,29 +458,42 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
   cudaError_t e = cudaSuccess;
   if (tuning || !b->cfg.use_graph) {
     e = enqueue(tuning);
-  } else {
-    // captured once per launch plan and replayed; the replay re-reads the
-    // staging tables, so only the plan (not the buffer parity) keys it
-    if (sig != b->graph_sig || !b->exec) {
-      if (b->exec) cudaGraphExecDestroy(b->exec);
-      if (b->graph) cudaGraphDestroy(b->graph);
-      b->exec = nullptr;
-      b->graph = nullptr;
-      b->graph_sig.clear();
-      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        const cudaError_t e2 = enqueue(false);
-        e = cudaStreamEndCapture(b->stream, &b->graph);
-        if (e == cudaSuccess) e = e2;
-      }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-      if (e == cudaSuccess) b->graph_sig = sig;
+  } else if (sig != b->graph_sig[buf] || !b->exec[buf]) {
+    // capture the new plan; update the instantiated graph of this parity in
+    // place where the update applies (same launches, new parameters), else
+    // instantiate it afresh
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e2 = enqueue(false);
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e2;
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    bool updated = false;
+    if (e == cudaSuccess && b->exec[buf]) {
+      cudaGraphExecUpdateResultInfo info{};
+      updated = cudaGraphExecUpdate(b->exec[buf], g, &info) == cudaSuccess;
+      if (!updated) {
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(b->exec[buf]);
+        b->exec[buf] = nullptr;
+      }
+    }
+    if (e == cudaSuccess && !updated) e = cudaGraphInstantiate(&b->exec[buf], g, 0);
+    if (b->graph[buf]) cudaGraphDestroy(b->graph[buf]);
+    b->graph[buf] = g;
+    if (e == cudaSuccess) b->graph_sig[buf] = sig;
+    else b->graph_sig[buf].clear();
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[buf], b->stream);
+  } else {
+    e = cudaGraphLaunch(b->exec[buf], b->stream);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(b->tick_ev[t % lb_rt_batch::kTickEvents], b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "batch tick");
   b->maps_dirty = false;
-  // the members' step counters and buffer parity
+  b->ticks = t + 1;
+  // the members' step counters, buffer parity and, for those that finish
+  // in this tick, the tick to wait for
   for (int s = 0; s < (int)b->slots.size(); ++s) {
     Member& m = b->slots[s];
     if (!m.used) continue;
@@ -413,6 +502,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     const long long take = std::min<long long>(rem, K);
     m.h->cur ^= (int)(take & 1);
     m.h->steps += take;
+    if (m.h->steps >= m.nsteps) m.done_tick = t;
   }
   if (tuning) {
     BCK(b, cudaStreamSynchronize(b->stream));
@@ -437,6 +527,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
 lb_rt_status lb_rt_batch_sync(lb_rt_batch* b) {
   if (!b) return LB_RT_EINVAL;
   BCK(b, cudaStreamSynchronize(b->stream));
+  flush_grave(b);  // nothing is in flight: released memory goes back now
   unsigned word = 0;
   BCK(b, cudaMemcpy(&word, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (word) return bfail(b, LB_RT_ETIMEDOUT, "device error word set by a batched step");
@@ -449,7 +540,7 @@ lb_rt_status lb_rt_batch_poll(lb_rt_batch* b, int* slots, int max, int* n) {
   int c = 0;
   for (int s = 0; s < (int)b->slots.size(); ++s) {
     const Member& m = b->slots[s];
-    if (m.used && m.h->steps >= m.nsteps) {
+    if (m.used && m.h->steps >= m.nsteps && tick_done(b, m.done_tick)) {
       if (c < max) slots[c] = s;
       ++c;
     }
@@ -463,6 +554,9 @@ lb_rt_status lb_rt_batch_moments(lb_rt_batch* b, int slot, float* E, float* F, f
   if (!b) return LB_RT_EINVAL;
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
     return bfail(b, LB_RT_EINVAL, "bad slot");
+  // the problem's ticks have to be complete (its own stream does not see them)
+  if (b->ticks > 0)
+    BCK(b, cudaEventSynchronize(b->tick_ev[(b->ticks - 1) % lb_rt_batch::kTickEvents]));
   lb_rt* h = b->slots[slot].h;
   const lb_rt_status st = lb_rt_moments(h, E, F, P, nullptr, ptr_kind);
   if (st != LB_RT_OK) return bfail(b, st, lb_rt_last_error(h));
@@ -480,10 +574,12 @@ lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot) {
   if (!b) return LB_RT_EINVAL;
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
     return bfail(b, LB_RT_EINVAL, "bad slot");
-  BCK(b, cudaStreamSynchronize(b->stream));
   Member& m = b->slots[slot];
-  lb_rt_destroy(m.h);
-  b->used -= m.bytes;
+  // its last tick may still run: the memory goes back at the next
+  // synchronisation (or when an admission needs it)
+  b->grave.push_back(m.h);
+  b->grave_bytes += m.bytes;
+  if (m.ready) cudaEventDestroy(m.ready);
   m = Member{};
   return LB_RT_OK;
 }

@@ -6,10 +6,13 @@ count); the loop admits every arrived request whose device buffers fit the
 batch's memory budget (first come, first served), keeps admitted problems
 resident, advances all of them together one tick at a time (one persistent
 kernel launch per direction group and step, replayed from a CUDA graph) and
-retires a problem as soon as it has run its steps.  Requests that arrive
-while others are on the GPU join at the next tick.  Reported: per-request
-time to solution (completion minus arrival), its p50/p99, and throughput in
-requests/s and site-direction updates/s.
+retires a problem as soon as the tick with its last step has completed.
+Ticks are pipelined: the loop enqueues the next tick while the previous one
+runs (the batch keeps two in flight), and admissions run on the problems'
+own streams meanwhile, so the device does not wait for the host between
+ticks.  Requests that arrive while others are on the GPU join at the next
+tick.  Reported: per-request time to solution (completion minus arrival),
+its p50/p99, and throughput in requests/s and site-direction updates/s.
 
 All stepping runs in liblbrt.so; this module schedules and marshals only.
 """
@@ -82,9 +85,12 @@ def serve(requests, *, storage=lbrt.LB_RT_F16_DEV, steps_per_tick=50, max_proble
                     time.sleep(max(0.0, min(0.01, pending[0]["arrival"] - now)))
                 continue
             max_active = max(max_active, len(active))
-            lbrt.lb_rt_batch_tick(b)
-            ticks += 1
-            lbrt.lb_rt_batch_sync(b)
+            if lbrt.lb_rt_batch_tick(b) > 0:
+                ticks += 1
+            else:
+                # every step of the admitted problems is enqueued: wait for
+                # the ticks in flight so that the finished ones can retire
+                lbrt.lb_rt_batch_sync(b)
             for slot in lbrt.lb_rt_batch_poll(b):
                 req, t_admit = active.pop(slot)
                 if keep_results:
