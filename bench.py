@@ -64,10 +64,12 @@ CSRC = os.path.join(ROOT, "paper_2007_05718_gb300", "csrc")
 # bench size where the summary says so) and the sources it was captured from
 PROFILES = {
     "c3_fp32": ("step_static_f32_diffusion256_162.md", ("kernels_tma.cu", "tma_common.cuh")),
-    "c3_fp16": ("step_static_f16_diffusion256_162.md", ("kernels_sc.cu", "tma_common.cuh")),
+    "c3_fp16": ("step_static_f16_diffusion256_162.md", ("kernels_tma16.cu", "tma_common.cuh")),
+    "c3_bf16": ("step_static_bf16_diffusion256_162.md", ("kernels_tma16.cu", "tma_common.cuh")),
     "c2_fp32": ("step_static_f32_sphere128_42.md", ("kernels_tma.cu", "tma_common.cuh")),
     "c2_fp16": ("step_static_f16_sphere128_42.md", ("kernels_sc.cu", "tma_common.cuh")),
     "c5_fp32": ("step_moving_f32_shear128_162.md", ("kernels_tma_moving.cu", "tma_common.cuh")),
+    "c5_fp16": ("step_moving_f16_shear128_162.md", ("kernels_tma16.cu", "tma_common.cuh")),
 }
 
 
