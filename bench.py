@@ -465,6 +465,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle samples")
     ap.add_argument("--e2e-steps", type=int, default=10, help="coupled steps of the end-to-end run")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched serving run")
+    ap.add_argument("--serving-requests", type=int, default=150,
+                    help="requests of the seed-20200711 stream served in the open-loop run (2000 = all)")
     ap.add_argument("--no-collision-modes", action="store_true",
                     help="skip the implicit / explicit / Lambda-5 timing")
     ap.add_argument("--no-sublines", action="store_true",
@@ -597,7 +599,7 @@ def main():
             line["collision_modes"] = {"error": str(e)[:300]}
     if not args.no_serving and ws == 1:
         try:
-            line["serving"] = serving_measurement()
+            line["serving"] = serving_measurement(n_open=args.serving_requests)
         except Exception as e:  # report, do not hide
             line["serving"] = {"error": str(e)[:300]}
     if not args.no_cpu_baseline:
