@@ -439,13 +439,19 @@ def serving_measurement(n_capacity=24, n_open=150, seed=20200711, steps_per_tick
     closed = W.serving_requests(n_capacity, seed=seed, rate=1e9)
     for r in closed:
         r["arrival"] = 0.0
-    rc = serve.serve(closed, steps_per_tick=steps_per_tick, max_problems=64)
+    # capacity with one launch per direction group and step, then with the
+    # autotuner free to pair the 42- and 162-direction groups in one launch
+    rs = serve.serve(closed, steps_per_tick=steps_per_tick, max_problems=64, pair_groups=0)
+    rc = serve.serve(closed, steps_per_tick=steps_per_tick, max_problems=64, pair_groups=2)
     cap = rc["throughput_req_s"]
     rate = 0.8 * cap
     stream = W.serving_requests(n_open, seed=seed, rate=rate)
     ro = serve.serve(stream, steps_per_tick=steps_per_tick, max_problems=64)
     return {
         "capacity_req_s": cap, "capacity_sd_s": rc["throughput_sd_s"],
+        "capacity_separate_launches_req_s": rs["throughput_req_s"],
+        "capacity_paired_ticks": rc["paired_ticks"], "capacity_ticks": rc["ticks"],
+        "paired_ticks": ro["paired_ticks"],
         "arrival_rate_req_s": rate, "requests": ro["requests"], "completed": ro["completed"],
         "p50_s": ro["p50_s"], "p99_s": ro["p99_s"], "throughput_req_s": ro["throughput_req_s"],
         "throughput_sd_s": ro["throughput_sd_s"], "max_concurrent": ro["max_concurrent"],

@@ -270,9 +270,14 @@ lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch);
  * kernel launch over the concatenated tiles of all its problems (Sec. 3.3
  * stream and collision per problem, exactly as lb_rt_step), and a tick (the
  * steps_per_tick steps of every group) is captured into a CUDA graph and
- * replayed while its launch plan is unchanged.  An autotuner picks, per
- * group, the z-chunk length of the tiles by timing the candidates on the
- * first ticks of a new set of problems.  Admission is by device memory: a
+ * replayed while its launch plan is unchanged.  Two groups whose direction
+ * counts differ (for instance 42 and 162 directions) can share ONE launch
+ * per step (pair_groups): the persistent grid is split between the two
+ * groups' tiles in proportion to their work, each CTA running its group's
+ * tile plan.  An autotuner picks, per group, the z-chunk length of the
+ * tiles by timing the candidates on the first ticks of a new set of
+ * problems, and (pair_groups = 2) whether the paired launch beats the two
+ * separate ones.  Admission is by device memory: a
  * problem is admitted when its buffers fit the batch's budget and a slot is
  * free; otherwise lb_rt_batch_admit returns LB_RT_EBUSY and the caller
  * retries after completed problems are released.  Batched problems have no
@@ -291,6 +296,10 @@ typedef struct {
   int use_graph;       /* 1: capture ticks into a CUDA graph */
   int autotune;        /* 1: time the tile z-chunk candidates on new sets of problems */
   void* stream;        /* cudaStream_t; NULL => the batch creates one */
+  int pair_groups;     /* two groups of different direction counts in one launch per step:
+                          0 never, 1 whenever their tile plans have a paired kernel (the 42-
+                          and 162-direction icosahedral sets, every storage), 2 when the
+                          autotuner measures it faster than separate launches */
 } lb_rt_batch_config;
 
 lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out);
@@ -344,6 +353,12 @@ lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot);
 /* The autotuner's current choice for the group of `slot`: z-chunk length
  * (planes per tile) and CTAs of its last persistent launch. */
 lb_rt_status lb_rt_batch_tuning(const lb_rt_batch* b, int slot, int* zchunk, int* ctas);
+
+/* Tile plan of the group of `slot`: directions per warp, planes per batch,
+ * and whether its last tick shared a launch with another group (1) or not
+ * (0).  Any output pointer may be NULL. */
+lb_rt_status lb_rt_batch_plan(const lb_rt_batch* b, int slot, int* dirs_per_warp,
+                              int* planes_per_batch, int* paired);
 
 /* Message of the batch's last error. */
 const char* lb_rt_batch_last_error(const lb_rt_batch* b);

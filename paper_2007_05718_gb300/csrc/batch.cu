@@ -2,8 +2,9 @@
 // independent static-fluid problems resident on one device, admitted by
 // device memory, grouped by direction table and advanced together with one
 // persistent kernel launch per group and step (the batched form of the
-// TMA-fed step kernels), a CUDA graph per launch plan and a z-chunk
-// autotuner.  The paper solves one problem at a time; this layer is the
+// TMA-fed step kernels) or one launch per step for two groups of different
+// direction counts, a CUDA graph per launch plan and an autotuner of the
+// z chunks and of the pairing.  The paper solves one problem at a time; this layer is the
 // library's own.
 #include <algorithm>
 #include <cstring>
@@ -41,6 +42,7 @@ struct Group {
   long long tuned_sites = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int ctas = 0;           // CTAs of the last launch
+  bool paired = false;    // the last tick ran the group in a launch shared with another group
 };
 
 constexpr int kZCandidates[] = {8, 16, 32, 64};
@@ -81,6 +83,15 @@ struct lb_rt_batch {
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   std::vector<long long> graph_sig[2];
+  // two groups in one launch (cfg.pair_groups): the groups of the pair, the
+  // resident CTAs per SM of the paired kernel, and the autotuner's choice
+  // (mode 2): -1 undecided, 0 separate launches, 1 paired launch, timed on
+  // one tick each and normalised per site-direction update
+  int pair_a = -1, pair_b = -1, pair_per_sm = 0;
+  int pair_choice = -1, pair_trial = 0;
+  long long pair_sites = 0;  // sites of the two groups when the choice was timed
+  double pair_cost[2] = {0.0, 0.0};
+  cudaEvent_t pev0 = nullptr, pev1 = nullptr;
   std::string msg;
 };
 
@@ -127,8 +138,15 @@ bool same_table(const Group& g, const lb_rt* h) {
          std::memcmp(&g.table, &h->table, sizeof(DirTable)) == 0;
 }
 
+// One launch of a tick: a group's problems of one step, and optionally a
+// second group's (b_*) in the same launch, its problems on CTAs ctas_a ..
+// ctas - 1.
 struct Launch {
   int group, first, nprob, ntiles, periodic;
+  long long sd = 0;  // site-direction updates of the launch's problems of `group`
+  int b_group = -1, b_first = 0, b_nprob = 0, b_ntiles = 0, b_periodic = 0;
+  long long b_sd = 0;
+  int ctas_a = 0, ctas = 0;
 };
 
 }  // namespace
@@ -139,6 +157,7 @@ lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out
   if (!cfg || !out) return LB_RT_EINVAL;
   *out = nullptr;
   if (cfg->max_problems < 1 || cfg->max_problems > LB_RT_BATCH_MAX || cfg->steps_per_tick < 1 ||
+      cfg->pair_groups < 0 || cfg->pair_groups > 2 ||
       (cfg->storage != LB_RT_F32 && cfg->storage != LB_RT_F16_DEV &&
        cfg->storage != LB_RT_BF16_DEV))
     return LB_RT_EINVAL;
@@ -169,6 +188,8 @@ lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(unsigned));
   for (int i = 0; i < lb_rt_batch::kTickEvents && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&b->tick_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->pev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->pev1);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -199,6 +220,8 @@ void lb_rt_batch_destroy(lb_rt_batch* b) {
   }
   for (cudaEvent_t ev : b->tick_ev)
     if (ev) cudaEventDestroy(ev);
+  if (b->pev0) cudaEventDestroy(b->pev0);
+  if (b->pev1) cudaEventDestroy(b->pev1);
   cudaFreeHost(b->h_maps);
   cudaFree(b->d_maps);
   cudaFree(b->d_err);
@@ -350,6 +373,59 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       tuning = true;
     }
   }
+  // pairing: exactly two groups with steps in this tick whose tile plans
+  // have a paired kernel share one launch per step (mode 1), or do so when
+  // the autotuner measured it faster (mode 2); never while z chunks are tuned
+  int pa = -1, pb = -1;
+  if (b->cfg.pair_groups && !tuning) {
+    std::vector<int> act;
+    for (int g = 0; g < G; ++g)
+      if (group_sd[g]) act.push_back(g);
+    if (act.size() == 2) {
+      const Group& g0 = b->groups[act[0]];
+      const Group& g1 = b->groups[act[1]];
+      const int st = b->cfg.storage;
+      if (static_batch_pair_supported(st, g0.dpt, g0.zc, g1.dpt, g1.zc)) {
+        pa = act[0];
+        pb = act[1];
+      } else if (static_batch_pair_supported(st, g1.dpt, g1.zc, g0.dpt, g0.zc)) {
+        pa = act[1];
+        pb = act[0];
+      }
+    }
+  }
+  if (pa >= 0 && (pa != b->pair_a || pb != b->pair_b)) {
+    const Group& A = b->groups[pa];
+    const Group& B = b->groups[pb];
+    int per_sm = 0;
+    cudaError_t e = occupancy_static_batch_pair(b->cfg.storage, A.dpt, A.zc, A.Ni / A.dpt, B.dpt,
+                                                B.zc, B.Ni / B.dpt, &per_sm);
+    if (e != cudaSuccess) return bcuda(b, e, "paired kernel occupancy");
+    b->pair_a = pa;
+    b->pair_b = pb;
+    b->pair_per_sm = per_sm;
+    b->pair_choice = -1;
+    b->pair_trial = 0;
+  }
+  if (pa >= 0 && b->pair_per_sm < 1) pa = pb = -1;
+  bool pair_timed = false;  // this tick is one of mode 2's two trials
+  if (pa >= 0 && b->cfg.pair_groups == 2) {
+    // timed again when the pair's sites have changed by more than 2x
+    long long sites = 0;
+    for (int g : {pa, pb})
+      for (int s : plan[0][g]) sites += b->slots[s].h->grid.sites;
+    if (b->pair_choice >= 0 && (sites > 2 * b->pair_sites || 2 * sites < b->pair_sites)) {
+      b->pair_choice = -1;
+      b->pair_trial = 0;
+    }
+    if (b->pair_choice < 0 && b->pair_trial == 0) b->pair_sites = sites;
+    if (b->pair_choice < 0) {
+      pair_timed = true;
+      if (b->pair_trial == 0) pa = pb = -1;  // first trial: separate launches
+    } else if (b->pair_choice == 0) {
+      pa = pb = -1;
+    }
+  }
   // descriptor tables [step][group members]
   size_t ndesc = 0;
   for (int k = 0; k < K; ++k)
@@ -377,6 +453,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
   sig.push_back((long long)ndesc);
   size_t at = 0;
   for (int k = 0; k < K; ++k) {
+    const size_t first_of_step = launches.size();
     for (int g = 0; g < G; ++g) {
       const auto& ms = plan[k][g];
       if (ms.empty()) continue;
@@ -401,16 +478,49 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
         d.ntiles = (h->grid.nx + 63) / 64 * h->grid.ny * d.nzc;
         d.budget_partials = nullptr;
         L.ntiles += d.ntiles;
+        L.sd += h->grid.sites * (long long)gr.Ni;
         if (h->grid.periodic[0] || h->grid.periodic[1] || h->grid.periodic[2]) L.periodic = 1;
         sig.push_back(s);
         sig.push_back(d.nzc);
       }
       launches.push_back(L);
-      sig.push_back(L.group);
-      sig.push_back(L.first);
-      sig.push_back(L.nprob);
-      sig.push_back(L.ntiles);
-      sig.push_back(L.periodic);
+    }
+    // both groups of the pair step at k: one launch, CTAs split so that
+    // both halves take about as long (site-direction updates per warp)
+    if (pa >= 0 && launches.size() == first_of_step + 2) {
+      Launch& L0 = launches[first_of_step];
+      const Launch L1 = launches[first_of_step + 1];
+      Launch A = L0.group == pa ? L0 : L1;
+      const Launch& Bl = L0.group == pa ? L1 : L0;
+      const Group& GA = b->groups[pa];
+      const Group& GB = b->groups[pb];
+      long long S = std::min<long long>((long long)b->pair_per_sm * b->sms,
+                                        (long long)A.ntiles + Bl.ntiles);
+      if (S >= 2) {
+        const double wa = (double)A.sd / (GA.Ni / GA.dpt), wb = (double)Bl.sd / (GB.Ni / GB.dpt);
+        long long ca = std::llround((double)S * wa / (wa + wb));
+        ca = std::max<long long>(1, std::min<long long>(ca, S - 1));
+        ca = std::min<long long>(ca, A.ntiles);
+        ca = std::max<long long>(ca, S - Bl.ntiles);
+        A.b_group = Bl.group;
+        A.b_first = Bl.first;
+        A.b_nprob = Bl.nprob;
+        A.b_ntiles = Bl.ntiles;
+        A.b_periodic = Bl.periodic;
+        A.b_sd = Bl.sd;
+        A.ctas_a = (int)ca;
+        A.ctas = (int)S;
+        launches.resize(first_of_step);
+        launches.push_back(A);
+      }
+    }
+    for (size_t i = first_of_step; i < launches.size(); ++i) {
+      const Launch& L = launches[i];
+      for (long long v : {(long long)L.group, (long long)L.first, (long long)L.nprob,
+                          (long long)L.ntiles, (long long)L.periodic, (long long)L.b_group,
+                          (long long)L.b_first, (long long)L.b_nprob, (long long)L.b_ntiles,
+                          (long long)L.ctas_a, (long long)L.ctas})
+        sig.push_back(v);
     }
   }
   // problems stepped for the first time: their admission (initial state,
@@ -421,8 +531,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     BCK(b, cudaStreamWaitEvent(b->stream, m.ready, 0));
     m.joined = true;
   }
-  // the tick's device work: table uploads, then one batched launch per
-  // group and step
+  // the tick's device work: table uploads, then the launches (per group when
+  // the z-chunk autotuner times groups, in step order otherwise)
   auto enqueue = [&](bool timed) -> cudaError_t {
     cudaError_t e = cudaSuccess;
     if (b->maps_dirty || !timed)
@@ -431,33 +541,63 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_desc, h_desc, sizeof(ProblemDesc) * ndesc, cudaMemcpyHostToDevice,
                           b->stream);
-    for (int g = 0; g < G && e == cudaSuccess; ++g) {
-      Group& gr = b->groups[g];
-      const bool time_it = timed && !gr.tuned && group_sd[g] > 0;
-      if (time_it) e = cudaEventRecord(gr.ev0, b->stream);
-      for (const Launch& L : launches) {
-        if (L.group != g || e != cudaSuccess) continue;
-        BatchLaunch B{};
-        B.table = d_desc + L.first;
-        B.nprob = L.nprob;
-        B.ntiles = L.ntiles;
-        B.N = gr.Ni;
-        B.dpt = gr.dpt;
-        B.zc = gr.zc;
-        B.storage = b->cfg.storage;
-        B.ctas = (int)std::min<long long>((long long)gr.per_sm * b->sms, L.ntiles);
-        B.periodic = L.periodic;
-        B.err = b->d_err;
-        gr.ctas = B.ctas;
-        e = launch_tma_static_batch(B, gr.table, b->stream);
+    auto batch_of = [&](int g, int first, int nprob, int ntiles, int periodic, int ctas) {
+      const Group& gr = b->groups[g];
+      BatchLaunch B{};
+      B.table = d_desc + first;
+      B.nprob = nprob;
+      B.ntiles = ntiles;
+      B.N = gr.Ni;
+      B.dpt = gr.dpt;
+      B.zc = gr.zc;
+      B.storage = b->cfg.storage;
+      B.ctas = ctas;
+      B.periodic = periodic;
+      B.err = b->d_err;
+      return B;
+    };
+    auto single = [&](const Launch& L) -> cudaError_t {
+      Group& gr = b->groups[L.group];
+      const int ctas = (int)std::min<long long>((long long)gr.per_sm * b->sms, L.ntiles);
+      gr.ctas = ctas;
+      gr.paired = false;
+      return launch_tma_static_batch(batch_of(L.group, L.first, L.nprob, L.ntiles, L.periodic, ctas),
+                                     gr.table, b->stream);
+    };
+    if (timed && tuning) {
+      for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        Group& gr = b->groups[g];
+        const bool time_it = !gr.tuned && group_sd[g] > 0;
+        if (time_it) e = cudaEventRecord(gr.ev0, b->stream);
+        for (const Launch& L : launches)
+          if (L.group == g && e == cudaSuccess) e = single(L);
+        if (e == cudaSuccess && time_it) e = cudaEventRecord(gr.ev1, b->stream);
       }
-      if (e == cudaSuccess && time_it) e = cudaEventRecord(gr.ev1, b->stream);
+      return e;
     }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(b->pev0, b->stream);
+    for (const Launch& L : launches) {
+      if (e != cudaSuccess) break;
+      if (L.b_group < 0) {
+        e = single(L);
+        continue;
+      }
+      Group& ga = b->groups[L.group];
+      Group& gb = b->groups[L.b_group];
+      const BatchLaunch A = batch_of(L.group, L.first, L.nprob, L.ntiles, L.periodic, L.ctas_a);
+      const BatchLaunch B =
+          batch_of(L.b_group, L.b_first, L.b_nprob, L.b_ntiles, L.b_periodic, L.ctas - L.ctas_a);
+      ga.ctas = L.ctas_a;
+      gb.ctas = L.ctas - L.ctas_a;
+      ga.paired = gb.paired = true;
+      e = launch_static_batch_pair(A, ga.table, B, gb.table, L.ctas_a, L.ctas, b->stream);
+    }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(b->pev1, b->stream);
     return e;
   };
   cudaError_t e = cudaSuccess;
-  if (tuning || !b->cfg.use_graph) {
-    e = enqueue(tuning);
+  if (tuning || pair_timed || !b->cfg.use_graph) {
+    e = enqueue(tuning || pair_timed);
   } else if (sig != b->graph_sig[buf] || !b->exec[buf]) {
     // capture the new plan; update the instantiated graph of this parity in
     // place where the update applies (same launches, new parameters), else
@@ -503,6 +643,15 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     m.h->cur ^= (int)(take & 1);
     m.h->steps += take;
     if (m.h->steps >= m.nsteps) m.done_tick = t;
+  }
+  if (pair_timed) {
+    BCK(b, cudaStreamSynchronize(b->stream));
+    float ms = 0.f;
+    BCK(b, cudaEventElapsedTime(&ms, b->pev0, b->pev1));
+    long long sd = 0;
+    for (int g = 0; g < G; ++g) sd += group_sd[g] * b->groups[g].Ni;
+    b->pair_cost[b->pair_trial] = sd ? ms / (double)sd : 0.0;
+    if (++b->pair_trial == 2) b->pair_choice = b->pair_cost[1] < b->pair_cost[0] ? 1 : 0;
   }
   if (tuning) {
     BCK(b, cudaStreamSynchronize(b->stream));
@@ -581,6 +730,16 @@ lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot) {
   b->grave_bytes += m.bytes;
   if (m.ready) cudaEventDestroy(m.ready);
   m = Member{};
+  return LB_RT_OK;
+}
+
+lb_rt_status lb_rt_batch_plan(const lb_rt_batch* b, int slot, int* dirs_per_warp,
+                              int* planes_per_batch, int* paired) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used) return LB_RT_EINVAL;
+  const Group& g = b->groups[b->slots[slot].group];
+  if (dirs_per_warp) *dirs_per_warp = g.dpt;
+  if (planes_per_batch) *planes_per_batch = g.zc;
+  if (paired) *paired = g.paired ? 1 : 0;
   return LB_RT_OK;
 }
 

@@ -60,17 +60,18 @@ struct DirConst {
 // PER: some problem of the launch has a periodic axis (ghost columns,
 // mirror rows and planes are written by the fast store path); all-vacuum
 // launches use the plain store loop.
-template <int MODE, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
-__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
-k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
-           const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
-           const DirTable t) {
+// The body runs on CTA `cta` of `ncta` persistent CTAs with G warps; PART:
+// the block belongs to a launch shared by two tile plans (k_step_f32_pair).
+template <int MODE, bool PER, int DPT, int ZC, int R, bool PART>
+__device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const ProblemDesc& one,
+                                              const ProblemDesc* __restrict__ table, int nprob,
+                                              int ntiles, unsigned* err, const DirTable& t,
+                                              const int cta, const int ncta, const int G) {
   constexpr bool BATCH = MODE == 1;
   constexpr bool MOM = MODE == 2;
   constexpr int SLOT = slot_floats<DPT, ZC>();
   static_assert(SLOT >= ZC * 4 * 64, "the partial moments must fit in a consumed slot");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
   __shared__ ProblemDesc pd[BATCH ? 2 : 1];
   // shared layout: ring [G][R][SLOT] | coef [ZC][5][64] | dirs [N] DirConst |
@@ -111,7 +112,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
   }
   if (g == 0 && lane == 0) *abort_flag = 0;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
+  cta_sync<PART>(32 * G);
   unsigned inert_mask = 0;  // padding directions of this warp
 #pragma unroll
   for (int k = 0; k < DPT; ++k) inert_mask |= dirs[i0 + k].inert ? 1u << k : 0u;
@@ -120,7 +121,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
   bool alive = true;
   int issued = 0, waited = 0;
   // issue cursor (tile, item), ahead of the consumer by up to R - 1 items
-  int is_t = blockIdx.x, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0;
+  int is_t = cta, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0;
   const CUtensorMap* is_map = &tmap1;
   auto issue_seek = [&]() {
     if (is_t < ntiles) {
@@ -155,7 +156,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
     ++issued;
     if (++is_m == is_M) {
       is_m = 0;
-      is_t += gridDim.x;
+      is_t += ncta;
       issue_seek();
     }
     return true;
@@ -186,7 +187,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
   int q = 0;   // items consumed
   int tk = 0;  // tiles taken by this CTA
   int cp = 0;  // problem of the current tile
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++tk) {
+  for (int ti = cta; ti < ntiles; ti += ncta, ++tk) {
     const ProblemDesc* Pp = &one;
     if constexpr (BATCH) {
       while (cp < nprob && ti >= table[cp].tile_start + table[cp].ntiles) ++cp;
@@ -200,7 +201,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
         for (int w = lane; w < (int)(sizeof(ProblemDesc) / 4); w += 32)
           reinterpret_cast<int*>(dst)[w] = src[w];
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       Pp = dst;
     }
     const ProblemDesc& P = *Pp;
@@ -295,7 +296,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
         p[64] = aY[j];
         p[96] = aZ[j];
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       // coefficient units: unit u = (plane u / 2, sites 32 (u % 2) .. + 31)
       for (int u = g; u < nunits; u += G) {
         const int j = u >> 1, f = ((u & 1) << 5) + lane;
@@ -343,7 +344,7 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
           }
         }
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       if (!BATCH && one.budget_partials && g < nunits) {
         bud_da += (double)bud_a;
         bud_db += (double)bud_b;
@@ -494,16 +495,48 @@ k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ Pr
       bsum[2 * g] = bud_da;
       bsum[2 * g + 1] = bud_db;
     }
-    __syncthreads();
+    cta_sync<PART>(32 * G);
     if (g == 0 && lane == 0) {
       double a = 0.0, b = 0.0;
       for (int w = 0; w < min(G, nunits); ++w) {
         a += bsum[2 * w];
         b += bsum[2 * w + 1];
       }
-      atomicAdd(one.budget_partials + 2 * blockIdx.x, a);
-      atomicAdd(one.budget_partials + 2 * blockIdx.x + 1, b);
+      atomicAdd(one.budget_partials + 2 * cta, a);
+      atomicAdd(one.budget_partials + 2 * cta + 1, b);
     }
+  }
+}
+
+template <int MODE, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
+k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
+           const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
+           const DirTable t) {
+  step_f32_body<MODE, PER, DPT, ZC, R, false>(tmap1, one, table, nprob, ntiles, err, t, blockIdx.x,
+                                              gridDim.x, blockDim.y);
+}
+
+// One batched launch over the problems of two groups with different tile
+// plans (the 42- and 162-direction icosahedral sets): CTAs 0 .. ctas_a - 1
+// walk group A's tiles with GA warps, the others group B's with GB warps;
+// the warps a plan does not use leave at once.  Per tile the arithmetic is
+// that of k_step_f32, so every problem gives the same bits as in its own
+// group's launch.
+template <bool PER, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
+k_step_f32_pair(const __grid_constant__ CUtensorMap unused, const __grid_constant__ ProblemDesc none,
+                const ProblemDesc* __restrict__ table_a, int nprob_a, int ntiles_a, int ga,
+                int ctas_a, const ProblemDesc* __restrict__ table_b, int nprob_b, int ntiles_b,
+                int gb, unsigned* err, const DirTable ta, const DirTable tb) {
+  if ((int)blockIdx.x < ctas_a) {
+    if ((int)threadIdx.y >= ga) return;
+    step_f32_body<1, PER, DA, ZA, R, true>(unused, none, table_a, nprob_a, ntiles_a, err, ta,
+                                           blockIdx.x, ctas_a, ga);
+  } else {
+    if ((int)threadIdx.y >= gb) return;
+    step_f32_body<1, PER, DB, ZB, R, true>(unused, none, table_b, nprob_b, ntiles_b, err, tb,
+                                           blockIdx.x - ctas_a, gridDim.x - ctas_a, gb);
   }
 }
 
@@ -629,6 +662,71 @@ cudaError_t launch_f32_batch(const BatchLaunch& B, const DirTable& t, cudaStream
 
 constexpr int kRing = 2;
 
+template <bool PER, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t set_smem_attr_pair() {
+  static unsigned long long attr_set = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_step_f32_pair<PER, DA, ZA, DB, ZB, R, MAXT, REGS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024 - 1024);
+  if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
+  return e;
+}
+
+template <int DA, int ZA, int DB, int ZB, int R>
+size_t pair_smem(int ga, int gb) {
+  return std::max(step_smem<DA, ZA, R>(ga), step_smem<DB, ZB, R>(gb));
+}
+
+template <int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t occupancy_pair(int ga, int gb, int* per_sm) {
+  int a = 0, b = 0;
+  const int threads = 32 * std::max(ga, gb);
+  cudaError_t e = set_smem_attr_pair<false, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_smem_attr_pair<true, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_f32_pair<false, DA, ZA, DB, ZB, R, MAXT, REGS>, threads,
+        pair_smem<DA, ZA, DB, ZB, R>(ga, gb));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_f32_pair<true, DA, ZA, DB, ZB, R, MAXT, REGS>, threads,
+        pair_smem<DA, ZA, DB, ZB, R>(ga, gb));
+  *per_sm = std::min(a, b);
+  return e;
+}
+
+template <int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t launch_f32_pair(const BatchLaunch& A, const DirTable& ta, const BatchLaunch& B,
+                            const DirTable& tb, int ctas_a, int ctas, cudaStream_t s) {
+  const int ga = A.N / DA, gb = B.N / DB;
+  if (ga < 1 || ga * DA != A.N || gb < 1 || gb * DB != B.N || 32 * std::max(ga, gb) > MAXT ||
+      ctas_a < 1 || ctas_a >= ctas || !A.table || !B.table || A.nprob < 1 || B.nprob < 1 ||
+      A.ntiles < 1 || B.ntiles < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = pair_smem<DA, ZA, DB, ZB, R>(ga, gb);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const bool per = A.periodic || B.periodic;
+  const cudaError_t e = per ? set_smem_attr_pair<true, DA, ZA, DB, ZB, R, MAXT, REGS>()
+                            : set_smem_attr_pair<false, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e != cudaSuccess) return e;
+  CUtensorMap unused{};
+  ProblemDesc none{};
+  const dim3 block(32, std::max(ga, gb));
+  if (per)
+    k_step_f32_pair<true, DA, ZA, DB, ZB, R, MAXT, REGS><<<ctas, block, smem, s>>>(
+        unused, none, A.table, A.nprob, A.ntiles, ga, ctas_a, B.table, B.nprob, B.ntiles, gb,
+        B.err, ta, tb);
+  else
+    k_step_f32_pair<false, DA, ZA, DB, ZB, R, MAXT, REGS><<<ctas, block, smem, s>>>(
+        unused, none, A.table, A.nprob, A.ntiles, ga, ctas_a, B.table, B.nprob, B.ntiles, gb,
+        B.err, ta, tb);
+  return cudaGetLastError();
+}
+
+
 // Dispatch over the compiled tile plans (directions per warp, planes per
 // batch, thread cap, registers per thread), in order of preference.  A
 // scheduler holds floor(16384 / (32 x registers)) warps: 96 registers allow
@@ -644,6 +742,11 @@ constexpr int kRing = 2;
   X(4, 1, 640, 96)
 
 }  // namespace
+
+// Plan pairs that share one batched launch (plan A, plan B, thread cap,
+// registers): the 42-direction (5 per warp, 2 planes) and the 162-direction
+// (11 per warp) icosahedral sets.
+#define LBRT_PAIR_PLANS(X) X(5, 2, 11, 1, 512, 128)
 
 #define LBRT_PLAN_ROW(D, Z, T, B) {D, Z, T},
 const int kTilePlans[][3] = {LBRT_TILE_PLANS(LBRT_PLAN_ROW)};
@@ -675,6 +778,39 @@ cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per
   LBRT_TILE_PLANS(LBRT_OCCB)
 #undef LBRT_OCCB
   return e;
+}
+
+bool static_batch_pair_supported(int storage, int dpt_a, int zc_a, int dpt_b, int zc_b) {
+  if (storage != ST_F32) return tma16_pair_supported(dpt_a, zc_a, dpt_b, zc_b);
+#define LBRT_PS(DA, ZA, DB, ZB, T, R_) \
+  if (dpt_a == DA && zc_a == ZA && dpt_b == DB && zc_b == ZB) return true;
+  LBRT_PAIR_PLANS(LBRT_PS)
+#undef LBRT_PS
+  return false;
+}
+
+cudaError_t launch_static_batch_pair(const BatchLaunch& A, const DirTable& ta, const BatchLaunch& B,
+                                     const DirTable& tb, int ctas_a, int ctas, cudaStream_t s) {
+  if (A.storage != B.storage) return cudaErrorInvalidValue;
+  if (A.storage != ST_F32) return launch_tma16_static_batch_pair(A, ta, B, tb, ctas_a, ctas, s);
+#define LBRT_LP(DA, ZA, DB, ZB, T, R_)                                                    \
+  if (A.dpt == DA && A.zc == ZA && B.dpt == DB && B.zc == ZB)                            \
+    return launch_f32_pair<DA, ZA, DB, ZB, kRing, T, R_>(A, ta, B, tb, ctas_a, ctas, s);
+  LBRT_PAIR_PLANS(LBRT_LP)
+#undef LBRT_LP
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_static_batch_pair(int storage, int dpt_a, int zc_a, int ga, int dpt_b,
+                                        int zc_b, int gb, int* per_sm) {
+  if (storage != ST_F32)
+    return occupancy_tma16_pair(storage, dpt_a, zc_a, ga, dpt_b, zc_b, gb, per_sm);
+#define LBRT_OP(DA, ZA, DB, ZB, T, R_)                                                    \
+  if (dpt_a == DA && zc_a == ZA && dpt_b == DB && zc_b == ZB)                            \
+    return occupancy_pair<DA, ZA, DB, ZB, kRing, T, R_>(ga, gb, per_sm);
+  LBRT_PAIR_PLANS(LBRT_OP)
+#undef LBRT_OP
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tma_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,

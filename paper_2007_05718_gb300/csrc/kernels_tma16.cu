@@ -86,18 +86,20 @@ __device__ __forceinline__ void store_e(float* e, const Grid& g, int z, int y, i
 // device array of problem descriptors walked by the persistent CTAs.
 // PER as in the float32 kernel: periodic axes take the fast store path
 // that also writes ghost columns and mirror rows / planes.
-template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
-__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
-k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUtensorMap emap1,
-          const __grid_constant__ ProblemDesc one, const ProblemDesc* __restrict__ table,
-          int nprob, int ntiles, unsigned* err, const DirTable t) {
+// The body runs on CTA `cta` of `ncta` persistent CTAs with G warps; PART:
+// the block belongs to a launch shared by two tile plans (k_step_16_pair).
+template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, bool PART>
+__device__ __forceinline__ void step16_body(const CUtensorMap& tmap1, const CUtensorMap& emap1,
+                                            const ProblemDesc& one,
+                                            const ProblemDesc* __restrict__ table, int nprob,
+                                            int ntiles, unsigned* err, const DirTable& t,
+                                            const int cta, const int ncta, const int G) {
   using C2 = Conv<ST>;
   using T2 = typename C2::T2;
   constexpr int SLOTB = slot_bytes16<DPT, ZC>();
   constexpr int ESLOT = eslot_floats<ZC>();
   static_assert(SLOTB >= ZC * 4 * 64 * 4, "the partial moments must fit in a consumed slot");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int G = blockDim.y;
   const int lane = threadIdx.x, g = threadIdx.y;
   __shared__ ProblemDesc pd[BATCH ? 2 : 1];
   // shared layout: ring [G][R][SLOTB] | E ring [R][ESLOT] | coef [ZC][5][64] |
@@ -142,7 +144,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
   }
   if (g == 0 && lane == 0) *abort_flag = 0;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
+  cta_sync<PART>(32 * G);
   unsigned inert_mask = 0;
 #pragma unroll
   for (int k = 0; k < DPT; ++k) inert_mask |= dirs[i0 + k].inert ? 1u << k : 0u;
@@ -150,7 +152,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
   unsigned char* my_ring = ring + (size_t)g * R * SLOTB;
   bool alive = true;
   int issued = 0, waited = 0;
-  int is_t = blockIdx.x, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0, is_y = 0,
+  int is_t = cta, is_p = 0, is_m = 0, is_M = 0, is_x0 = 0, is_yp = 0, is_zp = 0, is_y = 0,
       is_zb = 0;
   const CUtensorMap* is_map = &tmap1;
   const CUtensorMap* is_emap = &emap1;
@@ -196,7 +198,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
     ++issued;
     if (++is_m == is_M) {
       is_m = 0;
-      is_t += gridDim.x;
+      is_t += ncta;
       issue_seek();
     }
     return true;
@@ -229,7 +231,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
   int q = 0;
   int tk = 0;
   int cp = 0;
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++tk) {
+  for (int ti = cta; ti < ntiles; ti += ncta, ++tk) {
     const ProblemDesc* Pp = &one;
     if constexpr (BATCH) {
       while (cp < nprob && ti >= table[cp].tile_start + table[cp].ntiles) ++cp;
@@ -243,7 +245,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
         for (int w = lane; w < (int)(sizeof(ProblemDesc) / 4); w += 32)
           reinterpret_cast<int*>(dst)[w] = src[w];
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       Pp = dst;
     }
     const ProblemDesc& P = *Pp;
@@ -361,7 +363,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
         p[64] = aY[j];
         p[96] = aZ[j];
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       for (int u = g; u < nunits; u += G) {
         const int j = u >> 1, f = ((u & 1) << 5) + lane;
         const int x = x0 + f, z = zb + j;
@@ -402,7 +404,7 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
           if (alive) store_e(eout, gr, z, y, x, Eh);
         }
       }
-      __syncthreads();
+      cta_sync<PART>(32 * G);
       if (!BATCH && one.budget_partials && g < nunits) {
         bud_da += (double)bud_a;
         bud_db += (double)bud_b;
@@ -537,16 +539,49 @@ k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUt
       bsum[2 * g] = bud_da;
       bsum[2 * g + 1] = bud_db;
     }
-    __syncthreads();
+    cta_sync<PART>(32 * G);
     if (g == 0 && lane == 0) {
       double a = 0.0, b = 0.0;
       for (int w = 0; w < min(G, nunits); ++w) {
         a += bsum[2 * w];
         b += bsum[2 * w + 1];
       }
-      atomicAdd(one.budget_partials + 2 * blockIdx.x, a);
-      atomicAdd(one.budget_partials + 2 * blockIdx.x + 1, b);
+      atomicAdd(one.budget_partials + 2 * cta, a);
+      atomicAdd(one.budget_partials + 2 * cta + 1, b);
     }
+  }
+}
+
+template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
+k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUtensorMap emap1,
+          const __grid_constant__ ProblemDesc one, const ProblemDesc* __restrict__ table,
+          int nprob, int ntiles, unsigned* err, const DirTable t) {
+  step16_body<ST, BATCH, PER, DPT, ZC, R, false>(tmap1, emap1, one, table, nprob, ntiles, err, t,
+                                                 blockIdx.x, gridDim.x, blockDim.y);
+}
+
+// One batched launch over the problems of two groups with different tile
+// plans (for instance the 42- and the 162-direction icosahedral sets): CTAs
+// 0 .. ctas_a - 1 walk group A's tiles with GA warps, the others group B's
+// with GB warps.  The block has max(GA, GB) warps; the warps a plan does not
+// use leave at once.  Per tile the arithmetic is that of k_step_16, so every
+// problem gives the same bits as in its own group's launch.
+template <class ST, bool PER, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+__global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
+k_step_16_pair(const __grid_constant__ CUtensorMap unused, const __grid_constant__ ProblemDesc none,
+               const ProblemDesc* __restrict__ table_a, int nprob_a, int ntiles_a, int ga,
+               int ctas_a, const ProblemDesc* __restrict__ table_b, int nprob_b, int ntiles_b,
+               int gb, unsigned* err, const DirTable ta, const DirTable tb) {
+  if ((int)blockIdx.x < ctas_a) {
+    if ((int)threadIdx.y >= ga) return;
+    step16_body<ST, true, PER, DA, ZA, R, true>(unused, unused, none, table_a, nprob_a, ntiles_a,
+                                                err, ta, blockIdx.x, ctas_a, ga);
+  } else {
+    if ((int)threadIdx.y >= gb) return;
+    step16_body<ST, true, PER, DB, ZB, R, true>(unused, unused, none, table_b, nprob_b, ntiles_b,
+                                                err, tb, blockIdx.x - ctas_a, gridDim.x - ctas_a,
+                                                gb);
   }
 }
 
@@ -1108,6 +1143,73 @@ cudaError_t launch16_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t
 
 constexpr int kRing16 = 2;
 
+template <class ST, bool PER, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t set_smem_attr16_pair() {
+  static unsigned long long attr_set = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && (attr_set >> dev & 1ull)) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_step_16_pair<ST, PER, DA, ZA, DB, ZB, R, MAXT, REGS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+  if (e == cudaSuccess && dev < 64) attr_set |= 1ull << dev;
+  return e;
+}
+
+template <int DA, int ZA, int DB, int ZB, int R>
+size_t pair_smem16(int ga, int gb) {
+  return std::max(step_smem16<DA, ZA, R>(ga), step_smem16<DB, ZB, R>(gb));
+}
+
+template <class ST, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t occupancy16_pair(int ga, int gb, int* per_sm) {
+  int a = 0, b = 0;
+  const int threads = 32 * std::max(ga, gb);
+  cudaError_t e = set_smem_attr16_pair<ST, false, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e == cudaSuccess) e = set_smem_attr16_pair<ST, true, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, k_step_16_pair<ST, false, DA, ZA, DB, ZB, R, MAXT, REGS>, threads,
+        pair_smem16<DA, ZA, DB, ZB, R>(ga, gb));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_step_16_pair<ST, true, DA, ZA, DB, ZB, R, MAXT, REGS>, threads,
+        pair_smem16<DA, ZA, DB, ZB, R>(ga, gb));
+  *per_sm = std::min(a, b);
+  return e;
+}
+
+// A = the group of plan (DA, ZA), B = the group of plan (DB, ZB); CTAs
+// 0 .. ctas_a - 1 of the B.ctas-CTA grid take A's tiles.
+template <class ST, int DA, int ZA, int DB, int ZB, int R, int MAXT, int REGS>
+cudaError_t launch16_pair(const BatchLaunch& A, const DirTable& ta, const BatchLaunch& B,
+                          const DirTable& tb, int ctas_a, int ctas, cudaStream_t s) {
+  const int ga = A.N / DA, gb = B.N / DB;
+  if (ga < 1 || ga * DA != A.N || gb < 1 || gb * DB != B.N || 32 * std::max(ga, gb) > MAXT ||
+      ctas_a < 1 || ctas_a >= ctas || !A.table || !B.table || A.nprob < 1 || B.nprob < 1 ||
+      A.ntiles < 1 || B.ntiles < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = pair_smem16<DA, ZA, DB, ZB, R>(ga, gb);
+  if (smem > 226 * 1024) return cudaErrorInvalidValue;
+  const bool per = A.periodic || B.periodic;
+  const cudaError_t e = per ? set_smem_attr16_pair<ST, true, DA, ZA, DB, ZB, R, MAXT, REGS>()
+                            : set_smem_attr16_pair<ST, false, DA, ZA, DB, ZB, R, MAXT, REGS>();
+  if (e != cudaSuccess) return e;
+  CUtensorMap unused{};
+  ProblemDesc none{};
+  const dim3 block(32, std::max(ga, gb));
+  if (per)
+    k_step_16_pair<ST, true, DA, ZA, DB, ZB, R, MAXT, REGS><<<ctas, block, smem, s>>>(
+        unused, none, A.table, A.nprob, A.ntiles, ga, ctas_a, B.table, B.nprob, B.ntiles, gb,
+        B.err, ta, tb);
+  else
+    k_step_16_pair<ST, false, DA, ZA, DB, ZB, R, MAXT, REGS><<<ctas, block, smem, s>>>(
+        unused, none, A.table, A.nprob, A.ntiles, ga, ctas_a, B.table, B.nprob, B.ntiles, gb,
+        B.err, ta, tb);
+  return cudaGetLastError();
+}
+
+
 // Tile plans for 16-bit storage (directions per warp, planes per batch,
 // thread cap, registers per thread), in order of preference.  The decoded
 // energy densities of a batch take registers that the float32 kernel does
@@ -1137,6 +1239,32 @@ cudaError_t occupancy_typed(int dpt, int zc, int G, int* per_sm, bool batch) {
                  : occupancy16<ST, false, D, Z, kRing16, T, B>(G, per_sm);
   LBRT_TILE_PLANS16(LBRT_O16)
 #undef LBRT_O16
+  return cudaErrorInvalidValue;
+}
+
+// Plan pairs that share one batched launch (plan A, plan B, thread cap,
+// registers): the 42-direction (5 per warp) and the 162-direction (11 per
+// warp) icosahedral sets.
+#define LBRT_PAIR_PLANS16(X) X(5, 1, 11, 1, 512, 128)
+
+template <class ST>
+cudaError_t launch_typed_pair(const BatchLaunch& A, const DirTable& ta, const BatchLaunch& B,
+                              const DirTable& tb, int ctas_a, int ctas, cudaStream_t s) {
+#define LBRT_LP16(DA, ZA, DB, ZB, T, R_)                                                  \
+  if (A.dpt == DA && A.zc == ZA && B.dpt == DB && B.zc == ZB)                            \
+    return launch16_pair<ST, DA, ZA, DB, ZB, kRing16, T, R_>(A, ta, B, tb, ctas_a, ctas, s);
+  LBRT_PAIR_PLANS16(LBRT_LP16)
+#undef LBRT_LP16
+  return cudaErrorInvalidValue;
+}
+
+template <class ST>
+cudaError_t occupancy_typed_pair(int da, int za, int ga, int db, int zb, int gb, int* per_sm) {
+#define LBRT_OP16(DA, ZA, DB, ZB, T, R_)                                                  \
+  if (da == DA && za == ZA && db == DB && zb == ZB)                                      \
+    return occupancy16_pair<ST, DA, ZA, DB, ZB, kRing16, T, R_>(ga, gb, per_sm);
+  LBRT_PAIR_PLANS16(LBRT_OP16)
+#undef LBRT_OP16
   return cudaErrorInvalidValue;
 }
 
@@ -1202,6 +1330,31 @@ cudaError_t launch_tma16_moving(const StepLaunch& L, const MovingCoef& c, const 
 cudaError_t launch_tma16_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
   if (B.storage == ST_F16) return launch_typed_batch<__half>(B, t, s);
   if (B.storage == ST_BF16) return launch_typed_batch<__nv_bfloat16>(B, t, s);
+  return cudaErrorInvalidValue;
+}
+
+bool tma16_pair_supported(int da, int za, int db, int zb) {
+#define LBRT_PS16(DA, ZA, DB, ZB, T, R_) \
+  if (da == DA && za == ZA && db == DB && zb == ZB) return true;
+  LBRT_PAIR_PLANS16(LBRT_PS16)
+#undef LBRT_PS16
+  return false;
+}
+
+cudaError_t launch_tma16_static_batch_pair(const BatchLaunch& A, const DirTable& ta,
+                                           const BatchLaunch& B, const DirTable& tb, int ctas_a,
+                                           int ctas, cudaStream_t s) {
+  if (A.storage != B.storage) return cudaErrorInvalidValue;
+  if (A.storage == ST_F16) return launch_typed_pair<__half>(A, ta, B, tb, ctas_a, ctas, s);
+  if (A.storage == ST_BF16) return launch_typed_pair<__nv_bfloat16>(A, ta, B, tb, ctas_a, ctas, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_tma16_pair(int storage, int da, int za, int ga, int db, int zb, int gb,
+                                 int* per_sm) {
+  if (storage == ST_F16) return occupancy_typed_pair<__half>(da, za, ga, db, zb, gb, per_sm);
+  if (storage == ST_BF16)
+    return occupancy_typed_pair<__nv_bfloat16>(da, za, ga, db, zb, gb, per_sm);
   return cudaErrorInvalidValue;
 }
 

@@ -131,6 +131,22 @@ struct BatchLaunch {
 cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
 cudaError_t launch_tma16_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
 cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm);
+// Two groups with different tile plans in ONE batched launch: group A's
+// problems run on CTAs 0 .. ctas_a - 1 of the ctas-CTA grid, group B's on the
+// rest; a block has the warps of the larger plan.  Supported for the plan
+// pairs each storage type compiles (static_batch_pair_supported); A and B in
+// that pair's order.
+bool static_batch_pair_supported(int storage, int dpt_a, int zc_a, int dpt_b, int zc_b);
+cudaError_t launch_static_batch_pair(const BatchLaunch& A, const DirTable& ta, const BatchLaunch& B,
+                                     const DirTable& tb, int ctas_a, int ctas, cudaStream_t s);
+cudaError_t occupancy_static_batch_pair(int storage, int dpt_a, int zc_a, int ga, int dpt_b,
+                                        int zc_b, int gb, int* per_sm);
+bool tma16_pair_supported(int da, int za, int db, int zb);
+cudaError_t launch_tma16_static_batch_pair(const BatchLaunch& A, const DirTable& ta,
+                                           const BatchLaunch& B, const DirTable& tb, int ctas_a,
+                                           int ctas, cudaStream_t s);
+cudaError_t occupancy_tma16_pair(int storage, int da, int za, int ga, int db, int zb, int gb,
+                                 int* per_sm);
 
 // Kernel launchers.  Return cudaGetLastError() (or an error without
 // launching when the configuration is not supported).

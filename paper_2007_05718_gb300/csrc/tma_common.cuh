@@ -61,6 +61,19 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// CTA barrier.  A block that runs one tile plan uses __syncthreads(); a
+// block of a launch shared by two plans (kernels_tma16.cu, kernels_tma.cu)
+// has idle warps that leave at once, so its barriers are named barriers
+// counting the nthreads threads of the plan's warps.
+template <bool PART>
+__device__ __forceinline__ void cta_sync(int nthreads) {
+  if constexpr (PART) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
 constexpr int BOXX = 68;                          // columns x0 - 2 .. x0 + 65
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: longer is a fault
 

@@ -34,6 +34,7 @@ EXPORTED = [
     "lb_rt_batch_create", "lb_rt_batch_destroy", "lb_rt_batch_problem_bytes", "lb_rt_batch_admit",
     "lb_rt_batch_tick", "lb_rt_batch_sync", "lb_rt_batch_poll", "lb_rt_batch_moments",
     "lb_rt_batch_steps", "lb_rt_batch_release", "lb_rt_batch_tuning", "lb_rt_batch_last_error",
+    "lb_rt_batch_plan",
 ]
 
 
@@ -64,7 +65,7 @@ class lb_rt_fluid(C.Structure):
 class lb_rt_batch_config(C.Structure):
     _fields_ = [("mem_budget", C.c_size_t), ("max_problems", C.c_int), ("storage", C.c_int),
                 ("steps_per_tick", C.c_int), ("use_graph", C.c_int), ("autotune", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("pair_groups", C.c_int)]
 
 
 class lb_rt_budget(C.Structure):
@@ -129,6 +130,8 @@ def load(path=LIB_PATH):
         "lb_rt_batch_steps": (C.c_int, [H, C.c_int, C.POINTER(C.c_longlong)]),
         "lb_rt_batch_release": (C.c_int, [H, C.c_int]),
         "lb_rt_batch_tuning": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "lb_rt_batch_plan": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int)]),
         "lb_rt_batch_last_error": (C.c_char_p, [H]),
     }
     for name, (res, args) in sig.items():
@@ -434,11 +437,15 @@ def _bcheck(b, st):
 
 
 def lb_rt_batch_create(*, max_problems=64, storage=LB_RT_F16_DEV, steps_per_tick=10,
-                       mem_budget=0, use_graph=True, autotune=True, stream=None):
+                       mem_budget=0, use_graph=True, autotune=True, stream=None, pair_groups=0):
+    """pair_groups: 0 one launch per group and step, 1 two groups of different
+    direction counts share one launch per step where a paired kernel exists,
+    2 the autotuner chooses."""
     cfg = lb_rt_batch_config()
     cfg.mem_budget, cfg.max_problems, cfg.storage = mem_budget, max_problems, storage
     cfg.steps_per_tick, cfg.use_graph, cfg.autotune = steps_per_tick, int(use_graph), int(autotune)
     cfg.stream = stream or None
+    cfg.pair_groups = int(pair_groups)
     b = C.c_void_p()
     st = load().lb_rt_batch_create(C.byref(cfg), C.byref(b))
     if st != LB_RT_OK:
@@ -510,6 +517,13 @@ def lb_rt_batch_tuning(b, slot):
     c = C.c_int(0)
     _bcheck(b, load().lb_rt_batch_tuning(b, slot, C.byref(z), C.byref(c)))
     return z.value, c.value
+
+
+def lb_rt_batch_plan(b, slot):
+    """(directions per warp, planes per batch, paired) of the group of `slot`."""
+    d, z, p = C.c_int(0), C.c_int(0), C.c_int(0)
+    _bcheck(b, load().lb_rt_batch_plan(b, slot, C.byref(d), C.byref(z), C.byref(p)))
+    return d.value, z.value, p.value
 
 
 def lb_rt_batch_last_error(b):

@@ -46,20 +46,24 @@ def percentile(x, q):
 
 
 def serve(requests, *, storage=lbrt.LB_RT_F16_DEV, steps_per_tick=50, max_problems=64,
-          mem_budget=0, use_graph=True, autotune=True, keep_results=False, timeout_s=None):
+          mem_budget=0, use_graph=True, autotune=True, keep_results=False, timeout_s=None,
+          pair_groups=2):
     """Run the request stream (dicts with id, arrival [s], kind, n, ndir,
     kappa, steps) through one batch.  Arrival times are honoured on the wall
     clock from the call's start.  Returns a report dict; with keep_results
-    the final E [n^3] and F [3, n^3] of every request are included."""
+    the final E [n^3] and F [3, n^3] of every request are included.
+    pair_groups as lb_rt_batch_create: by default the autotuner decides
+    whether the 42- and 162-direction requests share one launch per step."""
     b = lbrt.lb_rt_batch_create(max_problems=max_problems, storage=storage,
                                 steps_per_tick=steps_per_tick, mem_budget=mem_budget,
-                                use_graph=use_graph, autotune=autotune)
+                                use_graph=use_graph, autotune=autotune, pair_groups=pair_groups)
     pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
     waiting = collections.deque()
     active = {}
     done = {}
     results = {}
     ticks = 0
+    paired_ticks = 0
     max_active = 0
     t0 = time.perf_counter()
     try:
@@ -87,6 +91,8 @@ def serve(requests, *, storage=lbrt.LB_RT_F16_DEV, steps_per_tick=50, max_proble
             max_active = max(max_active, len(active))
             if lbrt.lb_rt_batch_tick(b) > 0:
                 ticks += 1
+                if pair_groups and any(lbrt.lb_rt_batch_plan(b, s)[2] for s in active):
+                    paired_ticks += 1
             else:
                 # every step of the admitted problems is enqueued: wait for
                 # the ticks in flight so that the finished ones can retire
@@ -112,6 +118,7 @@ def serve(requests, *, storage=lbrt.LB_RT_F16_DEV, steps_per_tick=50, max_proble
     span = max((d["done"] for d in done.values()), default=wall) - t_first
     rep = {
         "requests": len(requests), "completed": len(done), "ticks": ticks,
+        "paired_ticks": paired_ticks,
         "max_concurrent": max_active, "wall_s": wall,
         "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
         "throughput_req_s": len(done) / span if span > 0 else None,

@@ -33,9 +33,13 @@ def _sphere(n, level, kappa_r, nsteps, shape=None):
                 fluid=dict(kappa_a=ka, eta=eta), state=E0, nsteps=nsteps, shape=shape)
 
 
-def _run_batch(reqs, storage, steps_per_tick=4, use_graph=True, autotune=True, mem_budget=0):
+def _run_batch(reqs, storage, steps_per_tick=4, use_graph=True, autotune=True, mem_budget=0,
+               pair_groups=0, plans=None):
+    """Run `reqs` to completion in one batch; `plans` (a list) receives, per
+    tick, each slot's (directions per warp, planes per batch, paired)."""
     b = lbrt.lb_rt_batch_create(max_problems=16, storage=storage, steps_per_tick=steps_per_tick,
-                                use_graph=use_graph, autotune=autotune, mem_budget=mem_budget)
+                                use_graph=use_graph, autotune=autotune, mem_budget=mem_budget,
+                                pair_groups=pair_groups)
     out = []
     try:
         slots = [lbrt.lb_rt_batch_admit(b, r["problem"], r["fluid"], r["state"],
@@ -44,6 +48,8 @@ def _run_batch(reqs, storage, steps_per_tick=4, use_graph=True, autotune=True, m
         for _ in range(10000):
             if lbrt.lb_rt_batch_tick(b) == 0:
                 break
+            if plans is not None:
+                plans.append([lbrt.lb_rt_batch_plan(b, s) for s in slots])
         lbrt.lb_rt_batch_sync(b)
         assert sorted(lbrt.lb_rt_batch_poll(b)) == sorted(slots)
         for r, s in zip(reqs, slots):
@@ -158,3 +164,28 @@ def test_batch_rejects_unsupported_problems(cuda):
             lbrt.lb_rt_batch_moments(b, 1, np.zeros(8, dtype=np.float32))
     finally:
         lbrt.lb_rt_batch_destroy(b)
+
+
+PAIR_STORAGES = [pytest.param(lbrt.LB_RT_F32, id="fp32"), pytest.param(lbrt.LB_RT_F16_DEV, id="fp16"),
+                 pytest.param(lbrt.LB_RT_BF16_DEV, id="bf16")]
+
+
+@pytest.mark.parametrize("storage", PAIR_STORAGES)
+@pytest.mark.parametrize("pair_groups", [1, 2])
+def test_paired_launch_equals_separate_launches(cuda, storage, pair_groups):
+    """42- and 162-direction problems stepped in ONE launch per step (each CTA
+    runs its own group's tile plan) give the bits of the separate launches;
+    with pair_groups = 1 every tick with both groups active is paired."""
+    reqs = _mix()
+    plans = []
+    # without the z-chunk tuner the first tick already pairs (the tuner
+    # times groups one launch each, and retunes a group whose sites shrink)
+    paired = _run_batch(reqs, storage, pair_groups=pair_groups, plans=plans, autotune=False)
+    sep = _run_batch(reqs, storage, pair_groups=0)
+    for (Ea, Fa), (Eb, Fb) in zip(paired, sep):
+        assert np.array_equal(Ea, Eb) and np.array_equal(Fa, Fb)
+    dpts = {p[0] for tick in plans for p in tick}
+    assert len(dpts) == 2                                   # two tile plans in the batch
+    if pair_groups == 1:
+        assert all(p[2] == 1 for p in plans[0])
+

@@ -51,7 +51,8 @@ int use_every_call(void) {
   long long steps = 0;
   int zc = 0, ctas = 0;
   st |= lb_rt_batch_moments(bt, slot, E, F, NULL, LB_RT_HOST) | lb_rt_batch_steps(bt, slot, &steps) |
-        lb_rt_batch_tuning(bt, slot, &zc, &ctas) | lb_rt_batch_release(bt, slot);
+        lb_rt_batch_tuning(bt, slot, &zc, &ctas) | lb_rt_batch_plan(bt, slot, &zc, &ctas, &n) |
+        lb_rt_batch_release(bt, slot);
   (void)lb_rt_batch_problem_bytes(bt, &cfg);
   (void)lb_rt_batch_last_error(bt);
   lb_rt_batch_destroy(bt);

@@ -147,12 +147,15 @@ def test_frozen_beam_injection(cuda):
     assert abs(b["injection"] - bo["injection"]) < 1e-4 * bo["injection"]
 
 
-def test_budget_matches_oracle_terms(cuda):
+@pytest.mark.parametrize("level", [1, 2])
+def test_budget_matches_oracle_terms(cuda, level):
+    """The FP64 budget of the 42- and the 162-direction tile plans."""
     shape = (6, 7, 33)
     coef = dict(kappa_a=W.random_fields(shape, 15, 0.0, 20.0), kappa_0=3.0, lam=0.2,
                 eta=W.random_fields(shape, 16, 0.0, 5.0))
-    p = Problem(3, shape, "ico", level=1, bc="vvv", coef=coef,
-                state=W.random_populations(42, shape, 17), budget=True)
+    ndir = 42 if level == 1 else 162
+    p = Problem(3, shape, "ico", level=level, bc="vvv", coef=coef,
+                state=W.random_populations(ndir, shape, 17), budget=True)
     I, E, F, b, Io, Eo, bo = _check(p, 3, f_scale="E")
     for k in ("outflow", "source"):
         assert abs(b[k] - bo[k]) < 1e-5 * abs(bo[k]) + 1e-6

@@ -97,6 +97,24 @@ def test_ragged_periodic_random_fields(cuda, collision):
     assert rel_l2(E1, E2) < 3e-6 and rel_l2(F1, F2) < 3e-6
 
 
+@pytest.mark.parametrize("bc", ["ppp", "vvv"])
+def test_162_directions_epilogue(cuda, bc):
+    """The E, F epilogue of the 162-direction tile plan (16 direction warps,
+    one plane per batch), periodic and vacuum faces."""
+    shape = (10, 12, 70)
+    co = dict(kappa_a=W.random_fields(shape, 21), kappa_0=W.random_fields(shape, 22, 0.5, 3.0),
+              eta=W.random_fields(shape, 23))
+    p = Problem(3, shape, "ico", level=2, cfl=0.5, bc=bc, coef=co,
+                state=W.random_populations(162, shape, 24))
+    E2, F2, I2 = _plain(p, 4)
+    E1, F1, I1 = _fused(p, 4, "device")
+    np.testing.assert_array_equal(I1, I2)
+    assert rel_l2(E1, E2) < 3e-6
+    assert np.linalg.norm(F1 - F2) / np.linalg.norm(E2) < 3e-6
+    _, Eo, Fo, _, _, _ = oracle_run(p, 4)
+    assert rel_l2(E1.reshape(p.shape), Eo) <= TOL_F32
+
+
 def test_2d_ring_with_forward_peaked_scattering(cuda):
     shape = (1, 24, 40)
     p = Problem(2, shape, "ring", ndir=16, ring_offset=0.3, cfl=0.7, bc="ppp",
