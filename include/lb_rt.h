@@ -274,10 +274,12 @@ lb_rt_status lb_rt_last_step_ms(lb_rt* h, float* ms, int* nlaunch);
  * counts differ (for instance 42 and 162 directions) can share ONE launch
  * per step (pair_groups): the persistent grid is split between the two
  * groups' tiles in proportion to their work, each CTA running its group's
- * tile plan.  An autotuner picks, per group, the z-chunk length of the
- * tiles by timing the candidates on the first ticks of a new set of
- * problems, and (pair_groups = 2) whether the paired launch beats the two
- * separate ones.  Admission is by device memory: a
+ * tile plan.  An autotuner picks, per group, the tile shape: the z-chunk
+ * length of the tiles, timed over the candidates on the first ticks of a
+ * new set of problems, then the planes per batch, where an alternative
+ * batched kernel of the same memory layout exists (the 42-direction plans);
+ * and (pair_groups = 2) whether the paired launch beats the two separate
+ * ones.  Every choice gives the same bits.  Admission is by device memory: a
  * problem is admitted when its buffers fit the batch's budget and a slot is
  * free; otherwise lb_rt_batch_admit returns LB_RT_EBUSY and the caller
  * retries after completed problems are released.  Batched problems have no
@@ -354,9 +356,10 @@ lb_rt_status lb_rt_batch_release(lb_rt_batch* b, int slot);
  * (planes per tile) and CTAs of its last persistent launch. */
 lb_rt_status lb_rt_batch_tuning(const lb_rt_batch* b, int slot, int* zchunk, int* ctas);
 
-/* Tile plan of the group of `slot`: directions per warp, planes per batch,
- * and whether its last tick shared a launch with another group (1) or not
- * (0).  Any output pointer may be NULL. */
+/* Tile plan of the group of `slot`: directions per warp, planes per batch
+ * of the batched kernel its last launch ran (the autotuner's choice, or its
+ * trial while tuning), and whether its last tick shared a launch with
+ * another group (1) or not (0).  Any output pointer may be NULL. */
 lb_rt_status lb_rt_batch_plan(const lb_rt_batch* b, int slot, int* dirs_per_warp,
                               int* planes_per_batch, int* paired);
 

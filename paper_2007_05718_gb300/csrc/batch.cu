@@ -4,7 +4,8 @@
 // persistent kernel launch per group and step (the batched form of the
 // TMA-fed step kernels) or one launch per step for two groups of different
 // direction counts, a CUDA graph per launch plan and an autotuner of the
-// z chunks and of the pairing.  The paper solves one problem at a time; this layer is the
+// tile shape (z chunks, planes per batch of the batched kernel) and of the
+// pairing.  The paper solves one problem at a time; this layer is the
 // library's own.
 #include <algorithm>
 #include <cstring>
@@ -43,6 +44,13 @@ struct Group {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int ctas = 0;           // CTAs of the last launch
   bool paired = false;    // the last tick ran the group in a launch shared with another group
+  // alternative batched kernel of the same layout (batch_alt_zc): its planes
+  // per batch (0: none) and residency; alt = 1 while it is in use.  The
+  // autotuner times it at the best z chunk after the z-chunk candidates.
+  int alt_zc = 0, alt_per_sm = 0, alt = 0;
+  int stage = 0;          // tuning: 0 z chunks, 1 the alternative kernel
+  int zc_now() const { return alt ? alt_zc : zc; }
+  int last_zc = 0;        // planes per batch of the kernel of the last launch
 };
 
 constexpr int kZCandidates[] = {8, 16, 32, 64};
@@ -70,7 +78,7 @@ struct lb_rt_batch {
   // synchronisation (freeing right away would wait for the ticks in flight)
   std::vector<lb_rt*> grave;
   size_t grave_bytes = 0;
-  // tensor maps of every slot: [slot][parity][pop, E]
+  // tensor maps of every slot: [slot][kernel variant][parity][pop, E]
   CUtensorMap* h_maps = nullptr;
   CUtensorMap* d_maps = nullptr;
   bool maps_dirty = true;
@@ -181,7 +189,7 @@ lb_rt_status lb_rt_batch_create(const lb_rt_batch_config* cfg, lb_rt_batch** out
     e = cudaMemGetInfo(&fr, &tot);
     b->budget = cfg->mem_budget ? cfg->mem_budget : (size_t)(0.8 * (double)fr);
   }
-  const size_t nmaps = (size_t)cfg->max_problems * 4;
+  const size_t nmaps = (size_t)cfg->max_problems * 8;
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_maps, sizeof(CUtensorMap) * nmaps);
   if (e == cudaSuccess) std::memset(b->h_maps, 0, sizeof(CUtensorMap) * nmaps);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_maps, sizeof(CUtensorMap) * nmaps);
@@ -297,7 +305,15 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
       return bcuda(b, e, "batched kernel occupancy");
     }
     for (int z : kZCandidates) g.cands.push_back(z);
-    g.cost.assign(g.cands.size(), 0.0);
+    g.cost.assign(g.cands.size() + 1, 0.0);  // z chunks, then the alternative kernel
+    g.alt_zc = batch_alt_zc(c.storage, g.dpt);
+    if (g.alt_zc &&
+        (occupancy_static_batch(c.storage, g.dpt, g.alt_zc, g.Ni / g.dpt, &g.alt_per_sm, 1) !=
+             cudaSuccess ||
+         g.alt_per_sm < 1)) {
+      (void)cudaGetLastError();
+      g.alt_zc = 0;
+    }
     if (!b->cfg.autotune) g.tuned = true;
     b->groups.push_back(g);
     gi = (int)b->groups.size() - 1;
@@ -320,10 +336,40 @@ lb_rt_status lb_rt_batch_admit(lb_rt_batch* b, const lb_rt_config* cfg, const lb
   m.joined = false;
   m.done_tick = -1;
   b->used += bytes;
-  // tensor maps of both parities, copied to the device array at the next tick
+  // a problem with fewer planes than the alternative kernel's batch keeps
+  // its group on the plan's own kernel
+  Group& grp = b->groups[gi];
+  if (grp.alt_zc && h->grid.nz < grp.alt_zc) {
+    grp.alt_zc = 0;
+    grp.alt = 0;
+    if (grp.stage == 1) {
+      grp.stage = 0;
+      grp.tuned = true;
+    }
+  }
+  // tensor maps of both parities (for the alternative kernel too, whose
+  // boxes hold its planes per batch), copied to the device array at the
+  // next tick
   for (int par = 0; par < 2; ++par) {
-    b->h_maps[(size_t)s * 4 + par * 2] = h->tmap[par];
-    if (c.storage != LB_RT_F32) b->h_maps[(size_t)s * 4 + par * 2 + 1] = h->emap[par];
+    CUtensorMap* mp = b->h_maps + (size_t)s * 8 + par * 2;
+    mp[0] = h->tmap[par];
+    if (c.storage != LB_RT_F32) mp[1] = h->emap[par];
+    if (grp.alt_zc) {
+      std::string terr;
+      const bool ok = c.storage == LB_RT_F32
+                          ? make_pop_tensor_map(mp + 4, h->grid, h->Ni, h->pop[par], h->dpt,
+                                                grp.alt_zc, terr)
+                          : make_pop16_tensor_map(mp + 4, h->grid, h->Ni, h->pop[par], c.storage,
+                                                  h->dpt, grp.alt_zc, terr) &&
+                                make_e_tensor_map(mp + 5, h->grid, h->ef[par], grp.alt_zc, terr);
+      if (!ok) {
+        m = Member{};
+        b->used -= bytes;
+        cudaEventDestroy(ready);
+        lb_rt_destroy(h);
+        return bfail(b, LB_RT_ECUDA, "tensor maps: " + terr);
+      }
+    }
   }
   b->maps_dirty = true;
   *slot = s;
@@ -366,10 +412,16 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
         (sites > 2 * gr.tuned_sites || 2 * sites < gr.tuned_sites)) {
       gr.tuned = false;
       gr.cand = 0;
+      gr.stage = 0;
     }
     if (!gr.tuned) {
-      gr.zchunk = gr.cands[gr.cand];
-      gr.tuned_sites = sites;
+      if (gr.stage == 0) {
+        gr.zchunk = gr.cands[gr.cand];
+        gr.alt = 0;
+        if (gr.cand == 0) gr.tuned_sites = sites;
+      } else {
+        gr.alt = 1;  // the alternative kernel at the best z chunk
+      }
       tuning = true;
     }
   }
@@ -385,10 +437,10 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       const Group& g0 = b->groups[act[0]];
       const Group& g1 = b->groups[act[1]];
       const int st = b->cfg.storage;
-      if (static_batch_pair_supported(st, g0.dpt, g0.zc, g1.dpt, g1.zc)) {
+      if (static_batch_pair_supported(st, g0.dpt, g0.zc_now(), g1.dpt, g1.zc_now())) {
         pa = act[0];
         pb = act[1];
-      } else if (static_batch_pair_supported(st, g1.dpt, g1.zc, g0.dpt, g0.zc)) {
+      } else if (static_batch_pair_supported(st, g1.dpt, g1.zc_now(), g0.dpt, g0.zc_now())) {
         pa = act[1];
         pb = act[0];
       }
@@ -398,8 +450,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     const Group& A = b->groups[pa];
     const Group& B = b->groups[pb];
     int per_sm = 0;
-    cudaError_t e = occupancy_static_batch_pair(b->cfg.storage, A.dpt, A.zc, A.Ni / A.dpt, B.dpt,
-                                                B.zc, B.Ni / B.dpt, &per_sm);
+    cudaError_t e = occupancy_static_batch_pair(b->cfg.storage, A.dpt, A.zc_now(), A.Ni / A.dpt,
+                                                B.dpt, B.zc_now(), B.Ni / B.dpt, &per_sm);
     if (e != cudaSuccess) return bcuda(b, e, "paired kernel occupancy");
     b->pair_a = pa;
     b->pair_b = pb;
@@ -467,8 +519,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
         d.g = h->grid;
         d.out = h->pop[cur ^ 1];
         d.e_out = h->ef[cur ^ 1];
-        d.tmap = b->d_maps + (size_t)s * 4 + cur * 2;
-        d.emap = b->d_maps + (size_t)s * 4 + cur * 2 + 1;
+        d.tmap = b->d_maps + (size_t)s * 8 + gr.alt * 4 + cur * 2;
+        d.emap = b->d_maps + (size_t)s * 8 + gr.alt * 4 + cur * 2 + 1;
         d.cf = h->sc;
         d.dt = (float)h->dt;
         d.collision = h->cfg.collision;
@@ -516,7 +568,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     }
     for (size_t i = first_of_step; i < launches.size(); ++i) {
       const Launch& L = launches[i];
-      for (long long v : {(long long)L.group, (long long)L.first, (long long)L.nprob,
+      for (long long v : {(long long)L.group, (long long)b->groups[L.group].alt,
+                          (long long)L.first, (long long)L.nprob,
                           (long long)L.ntiles, (long long)L.periodic, (long long)L.b_group,
                           (long long)L.b_first, (long long)L.b_nprob, (long long)L.b_ntiles,
                           (long long)L.ctas_a, (long long)L.ctas})
@@ -536,7 +589,7 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
   auto enqueue = [&](bool timed) -> cudaError_t {
     cudaError_t e = cudaSuccess;
     if (b->maps_dirty || !timed)
-      e = cudaMemcpyAsync(b->d_maps, b->h_maps, sizeof(CUtensorMap) * 4 * b->slots.size(),
+      e = cudaMemcpyAsync(b->d_maps, b->h_maps, sizeof(CUtensorMap) * 8 * b->slots.size(),
                           cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_desc, h_desc, sizeof(ProblemDesc) * ndesc, cudaMemcpyHostToDevice,
@@ -549,7 +602,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       B.ntiles = ntiles;
       B.N = gr.Ni;
       B.dpt = gr.dpt;
-      B.zc = gr.zc;
+      B.zc = gr.zc_now();
+      B.alt = gr.alt;
       B.storage = b->cfg.storage;
       B.ctas = ctas;
       B.periodic = periodic;
@@ -558,7 +612,9 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
     };
     auto single = [&](const Launch& L) -> cudaError_t {
       Group& gr = b->groups[L.group];
-      const int ctas = (int)std::min<long long>((long long)gr.per_sm * b->sms, L.ntiles);
+      const int per_sm = gr.alt ? gr.alt_per_sm : gr.per_sm;
+      const int ctas = (int)std::min<long long>((long long)per_sm * b->sms, L.ntiles);
+      gr.last_zc = gr.zc_now();
       gr.ctas = ctas;
       gr.paired = false;
       return launch_tma_static_batch(batch_of(L.group, L.first, L.nprob, L.ntiles, L.periodic, ctas),
@@ -589,6 +645,8 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
           batch_of(L.b_group, L.b_first, L.b_nprob, L.b_ntiles, L.b_periodic, L.ctas - L.ctas_a);
       ga.ctas = L.ctas_a;
       gb.ctas = L.ctas - L.ctas_a;
+      ga.last_zc = ga.zc_now();
+      gb.last_zc = gb.zc_now();
       ga.paired = gb.paired = true;
       e = launch_static_batch_pair(A, ga.table, B, gb.table, L.ctas_a, L.ctas, b->stream);
     }
@@ -660,13 +718,28 @@ lb_rt_status lb_rt_batch_tick(lb_rt_batch* b, int* n_active) {
       if (gr.tuned || !group_sd[g]) continue;
       float ms = 0.f;
       BCK(b, cudaEventElapsedTime(&ms, gr.ev0, gr.ev1));
+      const int nz = (int)gr.cands.size();
+      if (gr.stage == 1) {
+        // keep the alternative kernel only if it beat the best z chunk
+        gr.cost[nz] = ms / (double)group_sd[g];
+        double best = gr.cost[0];
+        for (int i = 1; i < nz; ++i) best = std::min(best, gr.cost[i]);
+        gr.alt = gr.cost[nz] < best ? 1 : 0;
+        gr.stage = 0;
+        gr.tuned = true;
+        continue;
+      }
       gr.cost[gr.cand] = ms / (double)group_sd[g];
-      if (++gr.cand == (int)gr.cands.size()) {
+      if (++gr.cand == nz) {
         int best = 0;
-        for (int i = 1; i < (int)gr.cands.size(); ++i)
+        for (int i = 1; i < nz; ++i)
           if (gr.cost[i] < gr.cost[best]) best = i;
         gr.zchunk = gr.cands[best];
-        gr.tuned = true;
+        if (gr.alt_zc) {
+          gr.stage = 1;
+        } else {
+          gr.tuned = true;
+        }
       }
     }
   }
@@ -738,7 +811,7 @@ lb_rt_status lb_rt_batch_plan(const lb_rt_batch* b, int slot, int* dirs_per_warp
   if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used) return LB_RT_EINVAL;
   const Group& g = b->groups[b->slots[slot].group];
   if (dirs_per_warp) *dirs_per_warp = g.dpt;
-  if (planes_per_batch) *planes_per_batch = g.zc;
+  if (planes_per_batch) *planes_per_batch = g.last_zc ? g.last_zc : g.zc_now();
   if (paired) *paired = g.paired ? 1 : 0;
   return LB_RT_OK;
 }

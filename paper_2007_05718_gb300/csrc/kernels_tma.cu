@@ -743,6 +743,13 @@ cudaError_t launch_f32_pair(const BatchLaunch& A, const DirTable& ta, const Batc
 
 }  // namespace
 
+// Alternative batched kernels (directions per warp, planes per batch, thread
+// cap, registers) with the memory layout of the tile plan of the same
+// directions per warp: the batch autotuner times them against the plan's
+// own kernel.  One plane per batch at 72 registers holds three 9-warp CTAs
+// per SM instead of two.
+#define LBRT_BATCH_ALT(X) X(5, 1, 320, 72)
+
 // Plan pairs that share one batched launch (plan A, plan B, thread cap,
 // registers): the 42-direction (5 per warp, 2 planes) and the 162-direction
 // (11 per warp) icosahedral sets.
@@ -761,8 +768,24 @@ size_t step_tile_smem(int dpt, int zc, int warps) {
   return (size_t)-1;
 }
 
+int batch_alt_zc(int storage, int dpt) {
+  if (storage != ST_F32) return batch_alt_zc16(dpt);
+#define LBRT_AZ(D, Z, T, R_) \
+  if (dpt == D) return Z;
+  LBRT_BATCH_ALT(LBRT_AZ)
+#undef LBRT_AZ
+  return 0;
+}
+
 cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
   if (B.storage != ST_F32) return launch_tma16_static_batch(B, t, s);
+  if (B.alt) {
+#define LBRT_LAUNCHA(D, Z, T, R_) \
+  if (B.dpt == D && B.zc == Z) return launch_f32_batch<D, Z, kRing, T, R_>(B, t, s);
+    LBRT_BATCH_ALT(LBRT_LAUNCHA)
+#undef LBRT_LAUNCHA
+    return cudaErrorInvalidValue;
+  }
 #define LBRT_LAUNCHB(D, Z, T, R_) \
   if (B.dpt == D && B.zc == Z) return launch_f32_batch<D, Z, kRing, T, R_>(B, t, s);
   LBRT_TILE_PLANS(LBRT_LAUNCHB)
@@ -770,9 +793,16 @@ cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cud
   return cudaErrorInvalidValue;
 }
 
-cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm) {
-  if (storage != ST_F32) return occupancy_tma16(storage, dpt, zc, G, per_sm, true);
+cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm, int alt) {
+  if (storage != ST_F32) return occupancy_tma16(storage, dpt, zc, G, per_sm, true, alt);
   cudaError_t e = cudaErrorInvalidValue;
+  if (alt) {
+#define LBRT_OCCA(D, Z, T, R_) \
+  if (dpt == D && zc == Z) e = occupancy<true, D, Z, kRing, T, R_>(G, per_sm);
+    LBRT_BATCH_ALT(LBRT_OCCA)
+#undef LBRT_OCCA
+    return e;
+  }
 #define LBRT_OCCB(D, Z, T, R_) \
   if (dpt == D && zc == Z) e = occupancy<true, D, Z, kRing, T, R_>(G, per_sm);
   LBRT_TILE_PLANS(LBRT_OCCB)

@@ -1231,8 +1231,22 @@ cudaError_t launch_typed(const StepLaunch& L, const StaticCoef& c, const DirTabl
   return cudaErrorInvalidValue;
 }
 
+// Alternative batched kernels (directions per warp, planes per batch, thread
+// cap, registers) with the memory layout of the tile plan of the same
+// directions per warp, timed by the batch autotuner against the plan's own
+// kernel: two planes per batch for the 42-direction plan, whose 128
+// registers hold one 9-warp CTA per SM instead of two.
+#define LBRT_BATCH_ALT16(X) X(5, 2, 320, 128)
+
 template <class ST>
-cudaError_t occupancy_typed(int dpt, int zc, int G, int* per_sm, bool batch) {
+cudaError_t occupancy_typed(int dpt, int zc, int G, int* per_sm, bool batch, int alt) {
+  if (alt) {
+#define LBRT_OA16(D, Z, T, B) \
+  if (dpt == D && zc == Z) return occupancy16<ST, true, D, Z, kRing16, T, B>(G, per_sm);
+    LBRT_BATCH_ALT16(LBRT_OA16)
+#undef LBRT_OA16
+    return cudaErrorInvalidValue;
+  }
 #define LBRT_O16(D, Z, T, B) \
   if (dpt == D && zc == Z)                                                              \
     return batch ? occupancy16<ST, true, D, Z, kRing16, T, B>(G, per_sm)                \
@@ -1270,6 +1284,13 @@ cudaError_t occupancy_typed_pair(int da, int za, int ga, int db, int zb, int gb,
 
 template <class ST>
 cudaError_t launch_typed_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s) {
+  if (B.alt) {
+#define LBRT_LA16(D, Z, T, R_) \
+  if (B.dpt == D && B.zc == Z) return launch16_batch<ST, D, Z, kRing16, T, R_>(B, t, s);
+    LBRT_BATCH_ALT16(LBRT_LA16)
+#undef LBRT_LA16
+    return cudaErrorInvalidValue;
+  }
 #define LBRT_LB16(D, Z, T, R_) \
   if (B.dpt == D && B.zc == Z) return launch16_batch<ST, D, Z, kRing16, T, R_>(B, t, s);
   LBRT_TILE_PLANS16(LBRT_LB16)
@@ -1299,9 +1320,17 @@ cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch) {
-  if (storage == ST_F16) return occupancy_typed<__half>(dpt, zc, G, per_sm, batch);
-  if (storage == ST_BF16) return occupancy_typed<__nv_bfloat16>(dpt, zc, G, per_sm, batch);
+int batch_alt_zc16(int dpt) {
+#define LBRT_AZ16(D, Z, T, R_) \
+  if (dpt == D) return Z;
+  LBRT_BATCH_ALT16(LBRT_AZ16)
+#undef LBRT_AZ16
+  return 0;
+}
+
+cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch, int alt) {
+  if (storage == ST_F16) return occupancy_typed<__half>(dpt, zc, G, per_sm, batch, alt);
+  if (storage == ST_BF16) return occupancy_typed<__nv_bfloat16>(dpt, zc, G, per_sm, batch, alt);
   return cudaErrorInvalidValue;
 }
 

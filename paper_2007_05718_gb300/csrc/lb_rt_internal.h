@@ -126,11 +126,18 @@ struct BatchLaunch {
   int N, dpt, zc, storage;
   int ctas;
   int periodic;              // some problem has a periodic axis
+  int alt;                   // 1: the alternative batched kernel of this dpt (batch_alt_zc)
   unsigned* err;
 };
 cudaError_t launch_tma_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
 cudaError_t launch_tma16_static_batch(const BatchLaunch& B, const DirTable& t, cudaStream_t s);
-cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm);
+cudaError_t occupancy_static_batch(int storage, int dpt, int zc, int G, int* per_sm, int alt = 0);
+// Planes per batch of the alternative batched kernel compiled for this storage
+// and directions-per-warp (same memory layout, other registers / planes per
+// batch, timed by the batch autotuner against the tile plan's own kernel), or
+// 0 when there is none.
+int batch_alt_zc(int storage, int dpt);
+int batch_alt_zc16(int dpt);
 // Two groups with different tile plans in ONE batched launch: group A's
 // problems run on CTAs 0 .. ctas_a - 1 of the ctas-CTA grid, group B's on the
 // rest; a block has the warps of the larger plan.  Supported for the plan
@@ -218,7 +225,8 @@ extern const int kTilePlans16[][3];
 extern const int kNumTilePlans16;
 cudaError_t launch_tma16_static(const StepLaunch& L, const StaticCoef& c, const DirTable& t,
                                 int storage, cudaStream_t s, int* nblocks);
-cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch = false);
+cudaError_t occupancy_tma16(int storage, int dpt, int zc, int G, int* per_sm, bool batch = false,
+                            int alt = 0);
 bool make_pop16_tensor_map(CUtensorMap* map, const Grid& g, int Ni, void* base, int storage, int dpt,
                            int zc, std::string& err);
 bool make_e_tensor_map(CUtensorMap* map, const Grid& g, float* base, int zc, std::string& err);

@@ -189,3 +189,20 @@ def test_paired_launch_equals_separate_launches(cuda, storage, pair_groups):
     if pair_groups == 1:
         assert all(p[2] == 1 for p in plans[0])
 
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_tuned_planes_per_batch_give_the_same_bits(cuda, storage):
+    """The autotuner times the alternative batched kernel of the 42-direction
+    plan (another number of planes per batch, same layout) after the z
+    chunks; the tick that runs it, and whatever it keeps, give the bits of
+    the single-problem path."""
+    reqs = [_sphere(24, 1, 10.0, 40), _sphere(0, 1, 0.0, 40, shape=(11, 17, 40)),
+            _sphere(20, 1, 1.0, 40)]
+    plans = []
+    res = _run_batch(reqs, storage, plans=plans)
+    zcs = {p[1] for tick in plans for p in tick}
+    assert len(zcs) == 2                        # both kernels ran (tick 4 times the other one)
+    for r, (E, F) in zip(reqs, res):
+        Es, Fs = _single(r, storage)
+        assert np.array_equal(E, Es) and np.array_equal(F, Fs)
