@@ -250,13 +250,19 @@ k_step_moving_tma(const __grid_constant__ CUtensorMap tmap, const StepLaunch L,
         const float4 s0 = d.s0, s1 = d.s1;
         const float2 ax = make_float2(s0.x, s0.y), ay = make_float2(s0.z, s0.w);
         const float2 az = make_float2(s1.x, s1.y);
-        const float* ownS = own + d.sh;
-        const float* upS = up + d.sh;
         const int off = k * BOXX;
         const float2 P0 = *reinterpret_cast<const float2*>(own + off);
-        const float2 S0 = make_float2(ownS[off], ownS[off + 1]);
         const float2 P1 = *reinterpret_cast<const float2*>(up + off);
-        const float2 S1 = make_float2(upS[off], upS[off + 1]);
+        // the x-upwind pair shares one value with the lane's own pair; one
+        // 4-byte load completes it (the x sign is uniform over the warp)
+        float2 S0, S1;
+        if (d.sh > 0) {
+          S0 = make_float2(P0.y, own[off + 2]);
+          S1 = make_float2(P1.y, up[off + 2]);
+        } else {
+          S0 = make_float2(own[off - 1], P0.x);
+          S1 = make_float2(up[off - 1], P1.x);
+        }
         const float2 X0 = f2fma(ax, f2sub(S0, P0), P0);
         const float2 X1 = f2fma(ax, f2sub(S1, P1), P1);
         const float2 Bn = f2fma(ay, f2sub(X1, X0), X0);
