@@ -28,6 +28,7 @@
 // lanes' sites, and I_i^{n+1} = alpha I*_i + w_i (c0 + n_i . c1) is stored as
 // float2 (plus ghost mirrors at periodic faces).
 #include <algorithm>
+#include <numeric>
 
 #include "lb_rt_internal.h"
 #include "tma_common.cuh"
@@ -62,7 +63,10 @@ struct DirConst {
 // launches use the plain store loop.
 // The body runs on CTA `cta` of `ncta` persistent CTAs with G warps; PART:
 // the block belongs to a launch shared by two tile plans (k_step_f32_pair).
-template <int MODE, bool PER, int DPT, int ZC, int R, bool PART>
+// XP: complete the x-upwind pair with one 4-byte shared load behind a branch
+// on the x sign (faster for vacuum faces and for periodic faces when the
+// grid rotates the CTAs over the x-blocks; see plan_static_grid).
+template <int MODE, bool PER, int DPT, int ZC, int R, bool PART, bool XP>
 __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const ProblemDesc& one,
                                               const ProblemDesc* __restrict__ table, int nprob,
                                               int ntiles, unsigned* err, const DirTable& t,
@@ -270,14 +274,15 @@ __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const Pr
           // Eq. (interp) as nested lerps: x on both rows, then y, then z
           // against the carried plane (B(z - 1) for sgn n^z = +1, B(z + 1)
           // otherwise, the box being shifted by one plane for the latter).
-          // The x-upwind pair shares one value with the lane's own pair: the
-          // all-vacuum kernel completes it with one more 4-byte load (3 %
-          // faster there), the periodic one loads both values (the branch
-          // made it 5 % slower)
+          // The x-upwind pair shares one value with the lane's own pair: with
+          // XP one more 4-byte load completes it (3 % faster for vacuum
+          // faces, 5 % with periodic faces when the CTAs rotate over the
+          // x-blocks); otherwise both values are loaded (the branch made the
+          // one-CTA-per-SM periodic kernel 5 % slower)
           const float2 P0 = *reinterpret_cast<const float2*>(own + off);
           const float2 P1 = *reinterpret_cast<const float2*>(up + off);
           float2 S0, S1;
-          if constexpr (PER) {
+          if constexpr (!XP) {
             S0 = make_float2(ownS[off], ownS[off + 1]);
             S1 = make_float2(upS[off], upS[off + 1]);
           } else if (xneg) {
@@ -527,8 +532,11 @@ __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
            const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
            const DirTable t) {
-  step_f32_body<MODE, PER, DPT, ZC, R, false>(tmap1, one, table, nprob, ntiles, err, t, blockIdx.x,
-                                              gridDim.x, blockDim.y);
+  // the one-load x pair: vacuum faces, or a single-problem plan with two or
+  // more CTAs per SM, whose periodic grid rotates the CTAs over the x-blocks
+  constexpr bool XP = !PER || (MODE != 1 && 2 * MAXT * REGS <= 65536);
+  step_f32_body<MODE, PER, DPT, ZC, R, false, XP>(tmap1, one, table, nprob, ntiles, err, t,
+                                                  blockIdx.x, gridDim.x, blockDim.y);
 }
 
 // One batched launch over the problems of two groups with different tile
@@ -545,11 +553,11 @@ k_step_f32_pair(const __grid_constant__ CUtensorMap unused, const __grid_constan
                 int gb, unsigned* err, const DirTable ta, const DirTable tb) {
   if ((int)blockIdx.x < ctas_a) {
     if ((int)threadIdx.y >= ga) return;
-    step_f32_body<1, PER, DA, ZA, R, true>(unused, none, table_a, nprob_a, ntiles_a, err, ta,
+    step_f32_body<1, PER, DA, ZA, R, true, !PER>(unused, none, table_a, nprob_a, ntiles_a, err, ta,
                                            blockIdx.x, ctas_a, ga);
   } else {
     if ((int)threadIdx.y >= gb) return;
-    step_f32_body<1, PER, DB, ZB, R, true>(unused, none, table_b, nprob_b, ntiles_b, err, tb,
+    step_f32_body<1, PER, DB, ZB, R, true, !PER>(unused, none, table_b, nprob_b, ntiles_b, err, tb,
                                            blockIdx.x - ctas_a, gridDim.x - ctas_a, gb);
   }
 }
@@ -896,14 +904,29 @@ cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const long long slots = (long long)per_sm * sms;
-  const long long txy = (long long)((g.nx + 63) / 64) * g.ny;
+  const int nxb = (g.nx + 63) / 64;
+  const long long txy = (long long)nxb * g.ny;
+  // With a periodic x axis the tiles of the first and last x-block also write
+  // the ghost columns.  Tiles are numbered x-block fastest and CTA b takes
+  // tiles b, b + C, ...: when C is a multiple of the x-blocks per row, every
+  // CTA keeps one x-block and the ghost-writing CTAs fall behind the others
+  // for the whole step.  A CTA count coprime to the x-blocks rotates every CTA
+  // through all x-blocks (measured with two CTAs per SM, 256^3 x 42 periodic:
+  // 2.09 -> 1.78 ms; with one CTA per SM the idle SM costs more than it saves).
+  const bool rotate = g.periodic[0] && per_sm >= 2 && nxb > 1;
+  auto grid_ctas = [&](long long nt) {
+    long long nc = std::min(nt, slots);
+    if (rotate)
+      while (nc > 1 && std::gcd(nc, (long long)nxb) > 1) --nc;
+    return nc;
+  };
   double best = 1e300;
   int best_c = 1;
   const int cmax = std::min(g.nz, 64);
   for (int c = 1; c <= cmax; ++c) {
     const long long nt = txy * c;
     if (nt > (1LL << 24)) break;
-    const long long nc = std::min(nt, slots);
+    const long long nc = grid_ctas(nt);
     const int base = g.nz / c, rem = g.nz % c;
     auto cost = [&](long long ti) {
       const long long ch = ti / txy;
@@ -922,7 +945,7 @@ cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage
     }
   }
   *nzc = best_c;
-  *ctas = (int)std::min<long long>(txy * best_c, slots);
+  *ctas = (int)grid_ctas(txy * best_c);
   return cudaSuccess;
 }
 
