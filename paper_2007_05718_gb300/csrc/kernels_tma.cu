@@ -66,7 +66,10 @@ struct DirConst {
 // XP: complete the x-upwind pair with one 4-byte shared load behind a branch
 // on the x sign (faster for vacuum faces and for periodic faces when the
 // grid rotates the CTAs over the x-blocks; see plan_static_grid).
-template <int MODE, bool PER, int DPT, int ZC, int R, bool PART, bool XP>
+// ROT: permute the x-blocks of each round of tiles (tile_rot); compiled in
+// for the single-problem plans of one CTA per SM, whose grid is a multiple of
+// the x-blocks (the plans of two or more CTAs per SM get a coprime grid).
+template <int MODE, bool PER, int DPT, int ZC, int R, bool PART, bool XP, bool ROT>
 __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const ProblemDesc& one,
                                               const ProblemDesc* __restrict__ table, int nprob,
                                               int ntiles, unsigned* err, const DirTable& t,
@@ -138,7 +141,9 @@ __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const Pr
         is_map = table[is_p].tmap;
       }
       const ProblemDesc& D = BATCH ? table[is_p] : one;
-      const TileGeom tg = tile_geom(is_t - D.tile_start, (D.g.nx + 63) / 64, D.g.ny, D.g.nz, D.nzc);
+      const int nxb_i = (D.g.nx + 63) / 64, rel_i = is_t - D.tile_start;
+      const TileGeom tg = tile_geom(rel_i, nxb_i, D.g.ny, D.g.nz, D.nzc,
+                                    ROT ? tile_rot(rel_i, nxb_i, ncta, D.g.periodic[0]) : 0);
       is_M = tile_items<ZC>(tg.zlen);
       is_x0 = tg.x0;
       is_yp = yneg ? tg.y + 1 : tg.y;  // lower padded row of the box
@@ -214,7 +219,9 @@ __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const Pr
     const float inv_d = 1.f / (float)gr.dims;
     float* __restrict__ out = static_cast<float*>(P.out);
     const StaticCoef& cf = P.cf;
-    const TileGeom tg = tile_geom(ti - P.tile_start, (nx + 63) / 64, ny, nz, P.nzc);
+    const int nxb_t = (nx + 63) / 64, rel_t = ti - P.tile_start;
+    const TileGeom tg = tile_geom(rel_t, nxb_t, ny, nz, P.nzc,
+                                  ROT ? tile_rot(rel_t, nxb_t, ncta, gr.periodic[0]) : 0);
     const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
     const int M = tile_items<ZC>(tg.zlen);
     const int xa = x0 + 2 * lane;  // the lane's pair (xa, xa + 1)
@@ -276,9 +283,9 @@ __device__ __forceinline__ void step_f32_body(const CUtensorMap& tmap1, const Pr
           // otherwise, the box being shifted by one plane for the latter).
           // The x-upwind pair shares one value with the lane's own pair: with
           // XP one more 4-byte load completes it (3 % faster for vacuum
-          // faces, 5 % with periodic faces when the CTAs rotate over the
-          // x-blocks); otherwise both values are loaded (the branch made the
-          // one-CTA-per-SM periodic kernel 5 % slower)
+          // faces, 3-5 % with periodic faces when the CTAs rotate over the
+          // x-blocks); otherwise both values are loaded (without the rotation
+          // the branch made the periodic kernel 5 % slower)
           const float2 P0 = *reinterpret_cast<const float2*>(own + off);
           const float2 P1 = *reinterpret_cast<const float2*>(up + off);
           float2 S0, S1;
@@ -532,11 +539,13 @@ __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_f32(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ ProblemDesc one,
            const ProblemDesc* __restrict__ table, int nprob, int ntiles, unsigned* err,
            const DirTable t) {
-  // the one-load x pair: vacuum faces, or a single-problem plan with two or
-  // more CTAs per SM, whose periodic grid rotates the CTAs over the x-blocks
-  constexpr bool XP = !PER || (MODE != 1 && 2 * MAXT * REGS <= 65536);
-  step_f32_body<MODE, PER, DPT, ZC, R, false, XP>(tmap1, one, table, nprob, ntiles, err, t,
-                                                  blockIdx.x, gridDim.x, blockDim.y);
+  // the one-load x pair: vacuum faces, or a single-problem launch, whose
+  // CTAs rotate over the x-blocks with a periodic x axis (a grid coprime to
+  // the x-blocks, or tile_rot); a batched launch does not rotate
+  constexpr bool XP = !PER || MODE != 1;
+  constexpr bool ROT = PER && MODE != 1 && 2 * MAXT * REGS > 65536;
+  step_f32_body<MODE, PER, DPT, ZC, R, false, XP, ROT>(tmap1, one, table, nprob, ntiles, err, t,
+                                                       blockIdx.x, gridDim.x, blockDim.y);
 }
 
 // One batched launch over the problems of two groups with different tile
@@ -553,11 +562,11 @@ k_step_f32_pair(const __grid_constant__ CUtensorMap unused, const __grid_constan
                 int gb, unsigned* err, const DirTable ta, const DirTable tb) {
   if ((int)blockIdx.x < ctas_a) {
     if ((int)threadIdx.y >= ga) return;
-    step_f32_body<1, PER, DA, ZA, R, true, !PER>(unused, none, table_a, nprob_a, ntiles_a, err, ta,
+    step_f32_body<1, PER, DA, ZA, R, true, !PER, false>(unused, none, table_a, nprob_a, ntiles_a, err, ta,
                                            blockIdx.x, ctas_a, ga);
   } else {
     if ((int)threadIdx.y >= gb) return;
-    step_f32_body<1, PER, DB, ZB, R, true, !PER>(unused, none, table_b, nprob_b, ntiles_b, err, tb,
+    step_f32_body<1, PER, DB, ZB, R, true, !PER, false>(unused, none, table_b, nprob_b, ntiles_b, err, tb,
                                            blockIdx.x - ctas_a, gridDim.x - ctas_a, gb);
   }
 }
@@ -912,7 +921,9 @@ cudaError_t plan_static_grid(const Grid& g, int Ni, int dpt, int zc, int storage
   // CTA keeps one x-block and the ghost-writing CTAs fall behind the others
   // for the whole step.  A CTA count coprime to the x-blocks rotates every CTA
   // through all x-blocks (measured with two CTAs per SM, 256^3 x 42 periodic:
-  // 2.09 -> 1.78 ms; with one CTA per SM the idle SM costs more than it saves).
+  // 2.09 -> 1.78 ms).  With one CTA per SM an idle SM costs more than it
+  // saves; those grids keep every SM and the static kernels permute the
+  // x-blocks of each round instead (tile_rot).
   const bool rotate = g.periodic[0] && per_sm >= 2 && nxb > 1;
   auto grid_ctas = [&](long long nt) {
     long long nc = std::min(nt, slots);

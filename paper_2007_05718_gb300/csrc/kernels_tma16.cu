@@ -88,7 +88,9 @@ __device__ __forceinline__ void store_e(float* e, const Grid& g, int z, int y, i
 // that also writes ghost columns and mirror rows / planes.
 // The body runs on CTA `cta` of `ncta` persistent CTAs with G warps; PART:
 // the block belongs to a launch shared by two tile plans (k_step_16_pair).
-template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, bool PART>
+// ROT: permute the x-blocks of each round of tiles (tile_rot), compiled in for
+// the single-problem plans of one CTA per SM.
+template <class ST, bool BATCH, bool PER, int DPT, int ZC, int R, bool PART, bool ROT>
 __device__ __forceinline__ void step16_body(const CUtensorMap& tmap1, const CUtensorMap& emap1,
                                             const ProblemDesc& one,
                                             const ProblemDesc* __restrict__ table, int nprob,
@@ -168,7 +170,9 @@ __device__ __forceinline__ void step16_body(const CUtensorMap& tmap1, const CUte
         is_emap = table[is_p].emap;
       }
       const ProblemDesc& D = BATCH ? table[is_p] : one;
-      const TileGeom tg = tile_geom(is_t - D.tile_start, (D.g.nx + 63) / 64, D.g.ny, D.g.nz, D.nzc);
+      const int nxb_i = (D.g.nx + 63) / 64, rel_i = is_t - D.tile_start;
+      const TileGeom tg = tile_geom(rel_i, nxb_i, D.g.ny, D.g.nz, D.nzc,
+                                    ROT ? tile_rot(rel_i, nxb_i, ncta, D.g.periodic[0]) : 0);
       is_M = tile_items<ZC>(tg.zlen);
       is_x0 = tg.x0;
       is_y = tg.y;
@@ -255,7 +259,9 @@ __device__ __forceinline__ void step16_body(const CUtensorMap& tmap1, const CUte
     ST* __restrict__ out = static_cast<ST*>(P.out);
     float* __restrict__ eout = P.e_out;
     const StaticCoef& cf = P.cf;
-    const TileGeom tg = tile_geom(ti - P.tile_start, (nx + 63) / 64, ny, nz, P.nzc);
+    const int nxb_t = (nx + 63) / 64, rel_t = ti - P.tile_start;
+    const TileGeom tg = tile_geom(rel_t, nxb_t, ny, nz, P.nzc,
+                                  ROT ? tile_rot(rel_t, nxb_t, ncta, gr.periodic[0]) : 0);
     const int x0 = tg.x0, y = tg.y, zbeg = tg.zbeg, zend = tg.zbeg + tg.zlen;
     const int M = tile_items<ZC>(tg.zlen);
     const int xa = x0 + 2 * lane;
@@ -557,8 +563,9 @@ __global__ void __launch_bounds__(MAXT) __maxnreg__(REGS)
 k_step_16(const __grid_constant__ CUtensorMap tmap1, const __grid_constant__ CUtensorMap emap1,
           const __grid_constant__ ProblemDesc one, const ProblemDesc* __restrict__ table,
           int nprob, int ntiles, unsigned* err, const DirTable t) {
-  step16_body<ST, BATCH, PER, DPT, ZC, R, false>(tmap1, emap1, one, table, nprob, ntiles, err, t,
-                                                 blockIdx.x, gridDim.x, blockDim.y);
+  constexpr bool ROT = PER && !BATCH && 2 * MAXT * REGS > 65536;
+  step16_body<ST, BATCH, PER, DPT, ZC, R, false, ROT>(tmap1, emap1, one, table, nprob, ntiles, err,
+                                                      t, blockIdx.x, gridDim.x, blockDim.y);
 }
 
 // One batched launch over the problems of two groups with different tile
@@ -575,11 +582,11 @@ k_step_16_pair(const __grid_constant__ CUtensorMap unused, const __grid_constant
                int gb, unsigned* err, const DirTable ta, const DirTable tb) {
   if ((int)blockIdx.x < ctas_a) {
     if ((int)threadIdx.y >= ga) return;
-    step16_body<ST, true, PER, DA, ZA, R, true>(unused, unused, none, table_a, nprob_a, ntiles_a,
+    step16_body<ST, true, PER, DA, ZA, R, true, false>(unused, unused, none, table_a, nprob_a, ntiles_a,
                                                 err, ta, blockIdx.x, ctas_a, ga);
   } else {
     if ((int)threadIdx.y >= gb) return;
-    step16_body<ST, true, PER, DB, ZB, R, true>(unused, unused, none, table_b, nprob_b, ntiles_b,
+    step16_body<ST, true, PER, DB, ZB, R, true, false>(unused, unused, none, table_b, nprob_b, ntiles_b,
                                                 err, tb, blockIdx.x - ctas_a, gridDim.x - ctas_a,
                                                 gb);
   }

@@ -178,9 +178,12 @@ __host__ __device__ constexpr int slot_floats() {
 struct TileGeom {
   int x0, y, zbeg, zlen;
 };
-__device__ __forceinline__ TileGeom tile_geom(int ti, int nxb, int ny, int nz, int nzc) {
+// rot: the x-blocks of the tile's row are permuted cyclically by rot (the
+// same rot for every tile of a row keeps the map a bijection).
+__device__ __forceinline__ TileGeom tile_geom(int ti, int nxb, int ny, int nz, int nzc,
+                                              int rot = 0) {
   TileGeom tg;
-  tg.x0 = (ti % nxb) * 64;
+  tg.x0 = ((ti % nxb + rot) % nxb) * 64;
   const int r = ti / nxb;
   tg.y = r % ny;
   const int c = r / ny;
@@ -195,6 +198,18 @@ __device__ __forceinline__ TileGeom tile_geom(int ti, int nxb, int ny, int nz, i
 // the output plane z = zbeg - 1 + m ZC + j (for both signs of n^z, with the
 // box shifted by one plane for sgn n^z = -1), which is stored when it lies in
 // the tile; the first plane of a tile only seeds the carried value.
+// Rotation of the x-blocks for tile ti (problem-relative) of a persistent
+// grid of ncta CTAs.  When ncta is a multiple of the x-blocks per row, CTA b
+// would keep one x-block for the whole step; with a periodic x axis the CTAs
+// of the first and last x-block also write the ghost columns and fall
+// behind.  Rotating the x-blocks of every row by the round ti / ncta makes
+// every CTA walk all x-blocks, while the tiles of one round (and so the
+// neighbouring rows in flight together) stay the same.  A row never spans
+// two rounds because ncta is a multiple of nxb.
+__device__ __forceinline__ int tile_rot(int ti, int nxb, int ncta, bool periodic_x) {
+  return (periodic_x && nxb > 1 && ncta % nxb == 0) ? ti / ncta : 0;
+}
+
 template <int ZC>
 __device__ __forceinline__ int tile_items(int zlen) {
   return (zlen + 1 + ZC - 1) / ZC;
