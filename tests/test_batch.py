@@ -1,8 +1,10 @@
 """Batched problems (lb_rt_batch_*): many independent static problems of
 uneven size and direction count advanced by one persistent launch per
-direction group and step.  Each result must equal the problem run alone
-(bit for bit: its tiles depend only on its own data), the single-problem
-library path, and the FP64 oracle within the storage's tolerance."""
+direction group and step, or one launch per step for a 42- and a
+162-direction group together (pair_groups), with the tile shape chosen by
+the autotuner.  Each result must equal the problem run alone (bit for bit:
+its tiles depend only on its own data), the single-problem library path,
+and the FP64 oracle within the storage's tolerance."""
 import numpy as np
 import pytest
 
