@@ -296,7 +296,7 @@ typedef struct {
   int storage;         /* LB_RT_F32 | LB_RT_F16_DEV | LB_RT_BF16_DEV, every problem */
   int steps_per_tick;  /* steps per lb_rt_batch_tick, >= 1 */
   int use_graph;       /* 1: capture ticks into a CUDA graph */
-  int autotune;        /* 1: time the tile z-chunk candidates on new sets of problems */
+  int autotune;        /* 1: time the tile shapes (z chunk, planes per batch) on new sets of problems */
   void* stream;        /* cudaStream_t; NULL => the batch creates one */
   int pair_groups;     /* two groups of different direction counts in one launch per step:
                           0 never, 1 whenever their tile plans have a paired kernel (the 42-
